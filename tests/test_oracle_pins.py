@@ -1,0 +1,432 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a library
+routine (networkx), a textbook closed form, exhaustive enumeration, an exact
+finite difference, a closed-form matrix power, or a fixed-point
+characterisation.  A dropped term, a wrong sign or a transposed operand in the
+oracle fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+from oracle import deco_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_graphs():
+    out = []
+    with open(os.path.join(GOLDEN, "maxcut_closed_forms.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            name, n, best = parts[0], int(parts[1]), int(parts[2])
+            us, vs = zip(*(tuple(map(int, e.split("-"))) for e in parts[3:]))
+            out.append((name, gg.from_edges(n, us, vs, name=name), best))
+    return out
+
+
+def _signed_random(n, p, seed):
+    g = gg.er_graph(n, p, seed)
+    rng = np.random.default_rng(seed + 99)
+    u, v, _ = g.edges()
+    w = rng.choice([-2.0, -1.0, 1.0, 3.0], size=u.size)
+    return gg.from_edges(n, u, v, w)
+
+
+# ---------------------------------------------------------------- cut (Eq. 1)
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_cut_matches_networkx(weighted):
+    nx = pytest.importorskip("networkx")
+    for seed in range(5):
+        g = _signed_random(30, 0.2, seed) if weighted else gg.er_graph(30, 0.2, seed)
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        u, v, w = g.edges()
+        for a, b, c in zip(u, v, w):
+            G.add_edge(int(a), int(b), weight=float(c))
+        z = gg.random_binary(g.n, 4, seed + 7)
+        for j in range(4):
+            S = [i for i in range(g.n) if z[i, j]]
+            ref = nx.cut_size(G, S, weight="weight" if weighted else None)
+            assert O.cut_value(g, z[:, j]) == int(round(ref))
+        assert list(O.cut_values(g, z)) == [O.cut_value(g, z[:, j]) for j in range(4)]
+
+
+@pytest.mark.parametrize("name,g,best", _golden_graphs(), ids=lambda x: x if isinstance(x, str) else "")
+def test_brute_force_closed_forms(name, g, best):
+    val, z = O.brute_force_maxcut(g)
+    assert val == best
+    assert O.cut_value(g, z) == best
+
+
+def test_brute_force_vs_subset_enumeration():
+    nx = pytest.importorskip("networkx")
+    for seed in range(3):
+        g = gg.er_graph(9, 0.4, seed)
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        u, v, _ = g.edges()
+        G.add_edges_from(zip(u.tolist(), v.tolist()))
+        ref = max(nx.cut_size(G, S) for r in range(g.n + 1)
+                  for S in itertools.combinations(range(g.n), r)) if g.m else 0
+        assert O.brute_force_maxcut(g)[0] == ref
+
+
+# ------------------------------------------------ objectives at binary points
+
+def test_vertex_identity_multilinear_and_laplacian():
+    for seed in range(4):
+        g = _signed_random(25, 0.3, seed)
+        z = gg.random_binary(g.n, 6, seed)
+        for j in range(6):
+            c = O.cut_value(g, z[:, j])
+            x = z[:, j].astype(np.float64)
+            assert O.objective_multilinear(g, x) == pytest.approx(c, abs=1e-9)
+            y = 2.0 * x - 1.0
+            assert O.objective_quco(g, y) == pytest.approx(4.0 * c, abs=1e-9)
+            # Eq. (3) summand with each unordered edge once: sum w (y_u - y_v)^2 = 4 Cut
+            u, v, w = g.edges()
+            assert float(np.sum(w * (y[u] - y[v]) ** 2)) == pytest.approx(4.0 * c, abs=1e-9)
+
+
+def test_laplacian_annihilates_constants():
+    # Lemma 2: L e_n = 0, so constant vectors are stationary.
+    g = _signed_random(40, 0.2, 3)
+    for c in (-1.0, 0.3, 1.0):
+        assert np.allclose(O.grad_quco(g, np.full(g.n, c)), 0.0, atol=1e-12)
+
+
+def test_laplacian_psd_unit_weights():
+    # Lemma 1: with non-negative weights L is PSD.
+    g = gg.er_graph(40, 0.2, 5)
+    ev = np.linalg.eigvalsh(O.laplacian(g).toarray())
+    assert ev.min() > -1e-9
+
+
+# ------------------------------------------------------- gradients (Eq. 6)
+
+def test_gradient_finite_difference():
+    rng = np.random.default_rng(0)
+    for seed in range(3):
+        g = _signed_random(20, 0.3, seed)
+        x = rng.uniform(0.0, 1.0, g.n)
+        y = rng.uniform(-1.0, 1.0, g.n)
+        gm = O.grad_multilinear(g, x)
+        gl = O.grad_quco(g, y)
+        h = 0.125
+        for v in range(g.n):
+            e = np.zeros(g.n)
+            e[v] = h
+            # F is affine in each coordinate: the central difference is exact
+            fd = (O.objective_multilinear(g, x + e) - O.objective_multilinear(g, x - e)) / (2 * h)
+            assert fd == pytest.approx(gm[v], abs=1e-9)
+            # f = y^T L y is quadratic: the central difference is exact and equals 2 L y
+            fd = (O.objective_quco(g, y + e) - O.objective_quco(g, y - e)) / (2 * h)
+            assert fd == pytest.approx(2.0 * gl[v], abs=1e-9)
+
+
+# ----------------------------------------- update rule in the box interior
+
+@pytest.mark.parametrize("objective", [O.OBJ_LAPLACIAN, O.OBJ_MULTILINEAR01])
+@pytest.mark.parametrize("mu", [0.0, 0.9])
+def test_interior_closed_form(objective, mu):
+    g = _signed_random(24, 0.3, 11)
+    rng = np.random.default_rng(1)
+    Y0 = rng.uniform(-1e-6, 1e-6, size=(g.n, 3))
+    alpha, T = 0.01, 12
+    A = O.adjacency(g).toarray()
+    L = O.laplacian(g).toarray()
+    I = np.eye(g.n)
+    if objective == O.OBJ_LAPLACIAN:
+        M, a = L, alpha              # V <- mu V + L Y ; Y <- Y + alpha V
+    else:
+        M, a = -A, 2.0 * alpha       # in y = 2x-1: V <- mu V - A Y ; Y <- Y + 2 alpha V
+    big = np.block([[I + a * M, a * mu * I], [M, mu * I]])
+    state = np.vstack([Y0, np.zeros_like(Y0)])
+    ref = np.linalg.matrix_power(big, T) @ state
+    Y, V = Y0.copy(), None
+    for _ in range(T):
+        Y, V = O.pga_step(g, Y, alpha, objective, V, mu)
+    assert np.max(np.abs(Y)) < 0.5          # stayed in the interior
+    # the multilinear oracle steps in x = (1+y)/2 ~ 0.5, whose FP64 spacing is
+    # 1.1e-16: compare there at that absolute precision (the entries are ~1e-6)
+    atol = 1e-18 if objective == O.OBJ_LAPLACIAN else 1e-13
+    np.testing.assert_allclose(Y, ref[: g.n], rtol=1e-9, atol=atol)
+    assert np.max(np.abs(ref[: g.n])) > 1e4 * atol
+
+
+def test_per_column_alpha_and_active_mask():
+    g = gg.er_graph(30, 0.2, 2)
+    rng = np.random.default_rng(3)
+    Y = rng.uniform(-1, 1, size=(g.n, 4))
+    a = np.array([0.01, 0.02, 0.03, 0.04])
+    Yn, _ = O.pga_step(g, Y, a, O.OBJ_MULTILINEAR01, active=np.array([1, 0, 1, 0], bool))
+    for j in range(4):
+        if j % 2:
+            assert np.array_equal(Yn[:, j], Y[:, j])
+        else:
+            ref, _ = O.pga_step(g, Y[:, j:j + 1], a[j], O.OBJ_MULTILINEAR01)
+            assert np.array_equal(Yn[:, j], ref[:, 0])
+
+
+# ----------------------------------------------- fixed points (Def. 2, Thm. 1)
+
+def test_paper_form_every_binary_is_fixed():
+    # Def. 2 / Sec. 3.1: for w >= 0, y_v (L y)_v = d_v - y_v (A y)_v >= 0 at binary
+    # y, so the projected step returns the same point for any alpha > 0.
+    g = gg.er_graph(10, 0.4, 1)
+    for code in range(1 << g.n):
+        y = np.array([1.0 if (code >> i) & 1 else -1.0 for i in range(g.n)])[:, None]
+        for alpha in (1e-3, 0.3, 5.0):
+            Yn, _ = O.pga_step(g, y, alpha, O.OBJ_LAPLACIAN)
+            assert np.array_equal(Yn, y)
+
+
+def test_multilinear_fixed_points_are_one_flip_optimal():
+    # In the multilinear form a binary x is unchanged by the projected step iff
+    # no single-vertex flip increases the cut (F is affine in each coordinate).
+    for seed in range(3):
+        g = _signed_random(9, 0.5, seed)
+        for code in range(1 << g.n):
+            z = np.array([(code >> i) & 1 for i in range(g.n)], dtype=np.uint8)
+            y = (2.0 * z - 1.0)[:, None]
+            Yn, _ = O.pga_step(g, y, 0.05, O.OBJ_MULTILINEAR01)
+            fixed = np.array_equal(Yn, y)
+            c = O.cut_value(g, z)
+            improving = False
+            for v in range(g.n):
+                z2 = z.copy()
+                z2[v] ^= 1
+                if O.cut_value(g, z2) > c:
+                    improving = True
+                    break
+            # a zero gain leaves the coordinate unchanged as well
+            assert fixed == (not improving)
+
+
+def test_multilinear_fixed_point_cut_at_least_half_edges():
+    for seed in range(3):
+        g = gg.er_graph(60, 0.1, seed)
+        Y = gg.uniform_x0(g.n, 8, seed) * 2.0 - 1.0
+        Y = O.run_phase(g, Y.astype(np.float64), O.Phase(1, 2000, 0.05), O.OBJ_MULTILINEAR01)
+        Z = O.binarize(Y)
+        binary = np.all(np.abs(Y) == 1.0, axis=0)
+        for j in np.flatnonzero(binary):
+            assert O.cut_value(g, Z[:, j]) * 2 >= g.m
+
+
+def test_lifted_constant_rows_round_to_cut_zero():
+    # Thm. 1 proof: X = e_n c^T rounds to a constant z, cut 0.
+    g = gg.er_graph(20, 0.3, 4)
+    for c in itertools.product([-1.0, 1.0], repeat=2):
+        X = np.tile(np.array(c), (g.n, 1))
+        z = O.binarize(X, 2)
+        assert len(set(z[:, 0])) == 1
+        assert O.cut_values(g, z)[0] == 0
+        Xn, _ = O.pga_step(g, X, 0.1, O.OBJ_LAPLACIAN)
+        assert np.array_equal(Xn, X)
+
+
+def test_lifted_columns_update_independently():
+    # Remark after Eq. (11): every column of X follows the unlifted update.
+    g = gg.er_graph(30, 0.2, 6)
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, size=(g.n, 6))
+    for obj in (O.OBJ_LAPLACIAN, O.OBJ_MULTILINEAR01):
+        Xn, _ = O.pga_step(g, X, 0.02, obj)
+        for j in range(6):
+            yj, _ = O.pga_step(g, X[:, j:j + 1], 0.02, obj)
+            np.testing.assert_array_equal(Xn[:, j], yj[:, 0])
+
+
+def test_binarize_strict_and_nonstrict():
+    Y = np.array([[0.0, 0.0], [1e-300, -1e-300], [-0.5, 0.5]])
+    assert O.binarize(Y, 1).tolist() == [[0, 0], [1, 0], [0, 1]]
+    # lifted: row sums 0, 0, 0 -> all >= 0
+    assert O.binarize(Y, 2).ravel().tolist() == [1, 1, 1]
+    assert O.binarize(np.array([[-1.0, 0.9]]), 2).ravel().tolist() == [0]
+
+
+def test_best_of_lowest_index():
+    assert O.best_of([3, 7, 7, 1]) == 1
+    assert O.best_of([5]) == 0
+
+
+# ------------------------------------------------------- initialisation
+
+def test_idi_star_is_optimal():
+    # a hub with k leaves: the hub is the only important node; every leaf sees
+    # the hub on one side and joins the other -> the cut is all k edges.
+    k = 12
+    g = gg.from_edges(k + 1, [0] * k, list(range(1, k + 1)))
+    imp = O.important_set(g, 0.2)
+    assert imp.tolist() == [True] + [False] * k
+    for seed in range(6):
+        h = O.idi_mean(g, seed)
+        z = (h > 0).astype(np.uint8)
+        assert O.cut_value(g, z) == k
+        assert np.all(h[1:] == -h[0])
+
+
+def test_idi_rule_on_hand_built_graph():
+    # two hubs 0 and 1 (degree 5); node 2 touches only hub 0, node 3 touches both,
+    # nodes 4..7 touch hub 1 and hub 0 as listed.
+    edges = [(0, 2), (0, 3), (1, 3), (0, 4), (1, 4), (1, 5), (1, 6), (0, 7)]
+    g = gg.from_edges(8, *zip(*edges))
+    imp = O.important_set(g, 0.2)
+    assert imp.tolist() == [True, True] + [False] * 6
+    for seed in range(16):
+        h = O.idi_mean(g, seed)
+        p0, p1 = h[0], h[1]
+        assert abs(p0) == 1 and abs(p1) == 1
+        assert h[2] == -p0 and h[7] == -p0 and h[5] == -p1 and h[6] == -p1
+        if p0 == p1:
+            assert h[3] == -p0 and h[4] == -p0
+        else:
+            assert abs(h[3]) == 1 and abs(h[4]) == 1   # ties: coin
+
+
+def test_idi_regular_graph_all_ties():
+    g = gg.torus_graph(6, 5, 0, signed=False)
+    assert not O.important_set(g).any()
+    hs = np.stack([O.idi_mean(g, s) for s in range(40)])
+    assert set(np.unique(hs)) == {-1.0, 1.0}
+    assert abs(hs.mean()) < 0.1
+
+
+def test_degree_moments_match_numpy():
+    g = gg.ba_graph(300, 4, 1)
+    deg = O.degree_count(g).astype(np.float64)
+    m, s = O.degree_moments(g)
+    assert m == pytest.approx(deg.mean(), rel=1e-15)
+    assert s == pytest.approx(deg.std(), rel=1e-12)
+
+
+def test_dui_range():
+    g = gg.ba_graph(200, 4, 2)
+    deg = O.degree_count(g)
+    h = O.dui_mean(g, 5)
+    hw = 1.0 - deg / deg.max()
+    assert np.all(np.abs(h) <= hw + 1e-15)
+    assert np.all(h[deg == deg.max()] == 0.0)
+    assert np.std(h / np.where(hw > 0, hw, 1)) > 0.4   # spread over the interval
+
+
+def test_philox_uniform_and_normal_distribution():
+    stats = pytest.importorskip("scipy.stats")
+    r = np.arange(400, dtype=np.uint64)[:, None]
+    c = np.arange(500, dtype=np.uint64)[None, :]
+    u = O.draw_uniform(r, c, 0, O.STREAM_INIT, 1234).ravel()
+    assert u.min() > 0.0 and u.max() < 1.0
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    z = O.draw_normal(r, c, 3, O.STREAM_INIT, 99).ravel()
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # distinct phases / streams / seeds give unrelated draws
+    u2 = O.draw_uniform(r, c, 1, O.STREAM_INIT, 1234).ravel()
+    u3 = O.draw_uniform(r, c, 0, O.STREAM_IDI, 1234).ravel()
+    u4 = O.draw_uniform(r, c, 0, O.STREAM_INIT, 1235).ravel()
+    for other in (u2, u3, u4):
+        assert abs(np.corrcoef(u, other)[0, 1]) < 0.01
+
+
+def test_philox_round_is_a_bijection():
+    # Each Philox round is invertible: lo words give c0, c2 back through the odd
+    # multipliers' inverses mod 2^32, then c1, c3 follow from the hi words.
+    rng = np.random.default_rng(0)
+    c = rng.integers(0, 2**32, size=(4, 1000), dtype=np.uint64)
+    k0, k1 = 0x12345678, 0x9ABCDEF0
+    # one round = philox with the key schedule truncated: compare 10 rounds of
+    # the oracle with a hand-inverted reconstruction round by round.
+    M0, M1 = 0xD2511F53, 0xCD9E8D57
+    inv0, inv1 = pow(M0, -1, 2**32), pow(M1, -1, 2**32)
+    out = O.philox4x32_10(c[0], c[1], c[2], c[3], k0, k1)
+    s = [x.astype(object) for x in out]
+    keys = [((k0 + r * 0x9E3779B9) & 0xFFFFFFFF, (k1 + r * 0xBB67AE85) & 0xFFFFFFFF) for r in range(10)]
+    for r in reversed(range(10)):
+        kk0, kk1 = keys[r]
+        n0, n1, n2, n3 = s
+        c2 = np.array([(int(x) * inv1) & 0xFFFFFFFF for x in n1], dtype=object)
+        c0 = np.array([(int(x) * inv0) & 0xFFFFFFFF for x in n3], dtype=object)
+        c1 = np.array([((int(a) * M1) >> 32) ^ int(b) ^ kk0 for a, b in zip(c2, n0)], dtype=object)
+        c3 = np.array([((int(a) * M0) >> 32) ^ int(b) ^ kk1 for a, b in zip(c0, n2)], dtype=object)
+        s = [c0, c1, c2, c3]
+    for i in range(4):
+        assert [int(x) for x in s[i]] == [int(x) for x in c[i]]
+
+
+def test_gaussian_block_scaling_and_clip():
+    g = gg.er_graph(50, 0.1, 0)
+    h = O.idi_mean(g, 3)
+    Y = O.gaussian_block(h, 64, 3, 0, 0.8, 1e-4)
+    assert np.all(np.abs(Y) <= 1.0)
+    # mean over columns tracks s*h, spread tracks s*sqrt(eta)
+    np.testing.assert_allclose(Y.mean(axis=1), 1e-4 * h, atol=1e-4 * 0.5)
+    assert Y.std() == pytest.approx(1e-4 * math.sqrt(1.0 * 0.8 + 1.0), rel=0.1)
+    big = O.gaussian_block(h, 64, 3, 0, 0.8, 10.0)
+    assert np.all(np.abs(big) <= 1.0) and np.any(np.abs(big) == 1.0)
+
+
+# ------------------------------------------------------------ evolution
+
+def test_evolution_rules():
+    rng = np.random.default_rng(0)
+    e = rng.uniform(-4, -1, 6)
+    T = rng.integers(3000, 10001, 6)
+    scores = np.array([5, 9, 1, 9, 3, 7])
+    eps = np.array([20.0, -20.0, 0.5])
+    epsp = np.array([0.0, 1.0, 0.5])
+    ne, nT, keep = O.evolve(e, T, scores, eps, epsp, 3000, 10000)
+    assert keep == [1, 3, 5]                 # top half, ties by lower index
+    for i in keep:
+        assert ne[i] == e[i] and nT[i] == T[i]
+    drop = [0, 4, 2][::-1]                    # scores 5,3,1 -> worst first is 2
+    worst_first = [2, 4, 0]
+    assert sorted(drop) == sorted(worst_first)
+    for j, victim in enumerate(worst_first):
+        src = keep[j]
+        assert -4.0 <= ne[victim] <= -1.0
+        assert ne[victim] == min(max(e[src] + 0.2 * eps[j], -4.0), -1.0)
+        assert nT[victim] == min(max(math.floor(T[src] * (1 + 0.2 * (2 * epsp[j] - 1))), 3000), 10000)
+    assert ne[worst_first[0]] == -1.0 and ne[worst_first[1]] == -4.0
+
+
+# -------------------------------------------------------------- solvers
+
+def test_solve_never_beats_brute_force_and_reports_consistently():
+    for seed in range(3):
+        g = gg.er_graph(16, 0.35, seed)
+        opt, _ = O.brute_force_maxcut(g)
+        res = O.solve(g, 16, [O.Phase(1, 150, 0.05, 0.9), O.Phase(2, 60, 0.01, 0.9),
+                              O.Phase(1, 150, 0.05, 0.9)],
+                      O.Params(objective=O.OBJ_LAPLACIAN, init="idi"), seed)
+        assert res.best_cut <= opt
+        assert res.best_cut == O.cut_value(g, res.assignment)
+        assert res.best_cut >= 0.8 * opt
+        for k, cuts in enumerate(res.phase_cuts):
+            assert cuts.max() <= res.best_cut
+
+
+def test_config1_shape_solve_runs():
+    g = gg.er_graph(100, 0.1, 0)
+    x0 = gg.uniform_x0(g.n, 64, 0)
+    res = O.solve(g, 64, [O.Phase(1, 500, 0.01, 0.0)],
+                  O.Params(objective=O.OBJ_MULTILINEAR01, init="explicit"), 0, x0=x0)
+    assert res.best_cut * 2 >= g.m
+    assert res.best_cut == O.cut_value(g, res.assignment)
+
+
+def test_greedy_half_guarantee():
+    for seed in range(3):
+        g = gg.er_graph(80, 0.1, seed)
+        z = O.greedy_maxcut(g, np.random.default_rng(seed).permutation(g.n))
+        assert 2 * O.cut_value(g, z) >= g.m
