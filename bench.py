@@ -1,0 +1,330 @@
+"""Benchmark of the DECO MaxCut hot path on one GB300 (or N replicas).
+
+Workload (one "step"): a full pDECO solve (Alg. 3) of two synthetic graphs,
+Erdos-Renyi G(800, 0.06) and a 40 x 20 torus with +-1 weights, each with
+B = 1024 starting points (512 IDI-centred Gaussian + 512 uniform), momentum
+0.9, schedule 2 x (800 unlifted steps alpha = 0.01 + 200 lifted steps l = 2
+alpha = 0.001), T = 2000; rounding, integer cuts and argmax after every phase.
+
+Metric: edge-updates/s = sum over phases of nnz * B * l * steps / seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl deco|reference]
+
+`--impl reference` times the CPU oracle (FP64, single thread) on a bounded
+sample of the same workload (the first phase, a slice of the starting
+points, a few steps) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "edge-updates/s (nnz x inits x iters / s)"
+WORKLOAD = "ER(n=800,p=0.06)+torus40x20(+-1); B=1024 (512 IDI + 512 uniform); pDECO T=2000 = 2x(800 unlifted a=0.01 + 200 lifted l=2 a=0.001), mu=0.9"
+B = 1024
+SCHEDULE = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9), (1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)]
+
+
+def graphs():
+    return [gg.er_graph(800, 0.06, 1), gg.torus_graph(40, 20, 2)]
+
+
+def edge_updates(gs, sched=SCHEDULE, b=B):
+    return sum(g.nnz * b * l * s for g in gs for (l, s, _, _) in sched)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_deco(args, rank, world):
+    import torch
+    import paper_2509_18612_gb300 as deco
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    gs = graphs()
+    handles = [deco.graph_from(g) for g in gs]
+    p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM,
+                    precision=deco.DECO_PREC_BF16 if args.precision == "bf16" else deco.DECO_PREC_FP32,
+                    polish_steps=args.polish if args.precision == "bf16" else 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    launches = [0]
+
+    def one_step(seed):
+        best = []
+        for G in handles:
+            res, _, _ = deco.deco_solve(G, B, SCHEDULE, p, seed, want_assignment=False,
+                                        want_phase_cuts=False, stream=stream)
+            best.append(res.best_cut)
+            launches[0] += res.kernel_launches
+        return best
+
+    for w in range(args.warmup):
+        one_step(1000 + w + 7919 * rank)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    cuts = []
+    launches[0] = 0
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()                                 # L2 flush between timed steps
+            ev[k][0].record(stream)
+            cuts.append(one_step(k + 7919 * rank))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    timed_launches = launches[0]
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    units = edge_updates(gs) * args.steps * world
+    value = units / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if rank == 0:
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for g in gs:
+            G = deco.graph_from(g)
+            res, z, pc = deco.deco_solve(G, B, SCHEDULE, p, 4242, stream=stream)
+            G.close()
+            h2d += g.row_ptr.nbytes + g.col_idx.nbytes + (0 if g.weights is None else g.nnz * 4)
+            d2h += z.nbytes + pc.nbytes + 32
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e = {"value": edge_updates(gs) / (t1 - t0), "unit": "edge-updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    roof = roofline_step(args, deco, torch, dev, handles[0], gs[0]) if rank == 0 else None
+
+    # ---- the other precision of the same workload (FP32 vs BF16-X/FP32-accum)
+    other = None
+    if rank == 0 and not args.no_other:
+        op = "fp32" if args.precision == "bf16" else "bf16"
+        p2 = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM,
+                         precision=deco.DECO_PREC_BF16 if op == "bf16" else deco.DECO_PREC_FP32,
+                         polish_steps=args.polish if op == "bf16" else 0)
+        for G in handles:
+            deco.deco_solve(G, B, SCHEDULE, p2, 99, want_assignment=False, want_phase_cuts=False, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        bc = []
+        for G in handles:
+            res, _, _ = deco.deco_solve(G, B, SCHEDULE, p2, 7, want_assignment=False, want_phase_cuts=False,
+                                        stream=stream)
+            bc.append(res.best_cut)
+        b.record(stream)
+        torch.cuda.synchronize()
+        other = {"dtype": op, "value": edge_updates(gs) / (a.elapsed_time(b) / 1e3),
+                 "polish_steps": args.polish if op == "bf16" else 0, "best_cuts": bc}
+    return {"value": value, "ms": ms, "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+            "best_cuts": cuts[-1], "gpu_launches": timed_launches, "other_precision": other}
+
+
+ROOF_STEPS = 800
+
+
+def roofline_step(args, deco, torch, dev, G, g):
+    """Dominant kernel: the persistent on-chip phase kernel (k_slab) running one
+    800-step unlifted phase of the ER graph over all C = 1024 columns, timed
+    with CUDA events on its launch stream (average over a few launches).
+
+    Algorithmic bytes per launch = steps x nnz x C x element size: every
+    stored CSR entry reads one neighbour's row segment from the on-chip
+    replica.  The bound is the SM load path (shared memory): 152 SMs x 128
+    bytes per clock."""
+    C = B
+    ld = C
+    prec = deco.DECO_PREC_BF16 if args.precision == "bf16" else deco.DECO_PREC_FP32
+    dt = torch.bfloat16 if args.precision == "bf16" else torch.float32
+    esz = 2 if args.precision == "bf16" else 4
+    y0 = (torch.rand(g.n, ld, device=dev) * 2e-4 - 1e-4).to(dt)
+    v = torch.zeros(g.n, ld, device=dev)
+    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, prec, 0.01, 0.9)
+    st = torch.cuda.current_stream()
+    y = y0.clone()
+    deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_ONCHIP, None, st)
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        y.copy_(y0)
+        v.zero_()
+        e0.record(st)
+        deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_ONCHIP, None, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
+    gathered = g.nnz * C * esz * ROOF_STEPS
+    compulsory = 2 * g.n * C * (esz + 4) + (g.n + 1 + g.nnz) * 4
+    peaks, kind = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_onchip = 152 * 128 * sm_mhz * 1e6 / 1e9      # GB/s through the SM load path
+    ach = gathered / t / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
+            "traffic": None, "kernel": "k_slab (persistent on-chip PGA phase, fused gather + step)",
+            "launch_us": t * 1e6, "steps_per_launch": ROOF_STEPS, "us_per_step": t * 1e6 / ROOF_STEPS,
+            "algorithmic_bytes_per_launch": gathered, "compulsory_dram_bytes_per_launch": compulsory,
+            "peak_kind": "derived: 152 SMs x 128 B/clk (shared-memory load path) x sm_max_mhz ("
+                         + kind + " clock)"}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle (FP64, one thread) on a bounded sample of the workload."""
+    from oracle import deco_oracle as O
+    gs = graphs()
+    cols = 64
+    steps = 10
+    sample_units = 0
+    t_total = 0.0
+    for _ in range(args.warmup and 1):
+        pass
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for g in gs:
+            Y = O.initial_block(g, cols, 1, O.Params(init="idi_half_uniform"), k)
+            O.run_phase(g, Y, O.Phase(1, steps, 0.01, 0.9), O.OBJ_MULTILINEAR01)
+            sample_units += g.nnz * cols * steps
+        t_total += time.perf_counter() - t0
+    value = sample_units / t_total
+    return {"value": value, "ms": t_total * 1e3 / max(args.steps, 1),
+            "sample": f"per step: first phase only, {cols} of {B} starting points, {steps} of 2000 steps, both graphs"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="deco", choices=["deco", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--polish", type=int, default=50)
+    ap.add_argument("--no-other", action="store_true", help="skip the other-precision measurement")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = run_reference(args, rank, world)
+        cores = 1
+        line = {"metric": METRIC, "value": r["value"], "unit": "edge-updates/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": r["value"], "unit": "edge-updates/s", "cores": cores,
+                                 "kind": "oracle", "sample": r["sample"]},
+                "e2e": {"value": r["value"], "unit": "edge-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    r = run_deco(args, rank, world)
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            rr = run_reference(argparse.Namespace(steps=1, warmup=0), 0, 1)
+            cpu = {"value": rr["value"], "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
+                   "sample": rr["sample"]}
+        line = {"metric": METRIC, "value": r["value"], "unit": "edge-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "clocks": r["clocks"], "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
+                "gpu_launches": r["gpu_launches"], "other_precision": r["other_precision"],
+                "best_cuts": r["best_cuts"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

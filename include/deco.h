@@ -1,0 +1,290 @@
+/*
+ * deco.h -- C ABI of the GB300 (sm_103a) hot path of the DECO MaxCut solver
+ * ("A Scalable Lift-and-Project Differentiable Approach For the Maximum Cut
+ * Problem", arXiv 2509.18612).
+ *
+ * The library computes batched projected gradient ascent (PGA) on the relaxed
+ * cut objective over an n x C block of starting points, alternating unlifted
+ * (Eq. QUCO, Alg. 1) and lifted (Eq. LUCO, Alg. 2) phases as in Alg. 3, then
+ * rounds every column (Eq. 5 / Eq. 11), evaluates integer cut values (Eq. 1)
+ * and takes the argmax over starting points.
+ *
+ * Conventions shared by every entry point
+ *  - All functions return an int status: DECO_OK (0) or a negative
+ *    deco_status code.  On error the outputs are left untouched and
+ *    deco_last_error() returns a message (thread-local).  No C++ exception
+ *    crosses this boundary.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory of the current device; "host" pointers are plain host memory.
+ *    The caller owns every buffer it passes in; the library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered; functions that return host results synchronise the
+ *    stream before returning.
+ *  - Iterates are stored in *centred* coordinates y in [-1,1], row-major
+ *    n x ld (column c of row v at y[v*ld + c]); ld >= C, ld % 8 == 0.
+ *    For the multilinear objective the paper-facing variable is x = (1+y)/2.
+ *    Columns of a lifted block are grouped per starting point: column
+ *    b*l + i holds component i of starting point b.
+ *  - Element types: DECO_PREC_FP32 -> float, DECO_PREC_BF16 -> 16-bit
+ *    bfloat16 (round to nearest even on store; all arithmetic in FP32).
+ */
+#ifndef DECO_H_
+#define DECO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DECO_ABI_VERSION 1
+
+typedef enum deco_status {
+  DECO_OK = 0,
+  DECO_ERR_ARG = -1,         /* invalid argument (NULL pointer, bad size, bad enum) */
+  DECO_ERR_GRAPH = -2,       /* malformed CSR (see deco_create_graph) */
+  DECO_ERR_OOM = -3,         /* device allocation failed */
+  DECO_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  DECO_ERR_NONFINITE = -5,   /* a non-finite value appeared in the iterate */
+  DECO_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  DECO_ERR_UNSUPPORTED = -7  /* valid request this build does not implement */
+} deco_status;
+
+/* Objectives (both in centred coordinates y in [-1,1]^n).
+ * DECO_OBJ_MULTILINEAR01: F(x) = sum_{(i,j) in E} w_ij (x_i + x_j - 2 x_i x_j)
+ *   on x in [0,1]^n, gradient d - 2 A x; the step
+ *   x <- Proj[0,1](x + alpha (d - 2 A x)) equals y <- Proj[-1,1](y - 2 alpha A y).
+ * DECO_OBJ_LAPLACIAN: f(x) = x^T L x on [-1,1]^n (Eq. QUCO), g = L x (Eq. 6),
+ *   step x <- Proj[-1,1](x + alpha L x) (Eq. 7; Eq. 10 per column when lifted). */
+#define DECO_OBJ_MULTILINEAR01 0
+#define DECO_OBJ_LAPLACIAN 1
+
+#define DECO_PREC_FP32 0
+#define DECO_PREC_BF16 1
+
+/* Initialisation of the first phase (Sec. 4.1, 4.2 and 5 of the paper).
+ *  UNIFORM          y = h * (2u - 1), u ~ U(0,1), h = uniform_half_width
+ *  IDI              Gaussian around h_IDI (Sec. 4.1.2)
+ *  DUI              Gaussian around h_DUI (Eq. 12)
+ *  IDI_HALF_UNIFORM starting points [0, B/2) as IDI, [B/2, B) as
+ *                   scale * (2u - 1)
+ *  EXPLICIT         caller-given x0 in the objective's own domain
+ *                   ([0,1] multilinear, [-1,1] Laplacian)
+ *  MEAN             Gaussian around a caller-given mean h (device, n floats)
+ * "Gaussian around h": y = Proj[-1,1](scale * (h_v + sqrt(eta) * N(0,1))).
+ * Every later phase is Gaussian around 2 z* - 1, z* the previous phase's best
+ * binary vector (Sec. 4.2; Alg. 3). */
+#define DECO_INIT_UNIFORM 0
+#define DECO_INIT_IDI 1
+#define DECO_INIT_DUI 2
+#define DECO_INIT_IDI_HALF_UNIFORM 3
+#define DECO_INIT_EXPLICIT 4
+#define DECO_INIT_MEAN 5
+
+/* Kernel used for the steps of a phase.
+ *  AUTO    the persistent on-chip kernel when a 128-byte column slab of the
+ *          graph (plus its share of the CSR) fits in shared memory, else one
+ *          launch of the global-memory kernel per step
+ *  GLOBAL  always the per-step global-memory kernel
+ *  ONCHIP  always the persistent on-chip kernel (DECO_ERR_UNSUPPORTED if it
+ *          does not fit)
+ * Both kernels perform the same FP32 operations in the same order, so their
+ * iterates are bit-identical. */
+#define DECO_KERNEL_AUTO 0
+#define DECO_KERNEL_GLOBAL 1
+#define DECO_KERNEL_ONCHIP 2
+/* With DECO_KERNEL_ONCHIP, DECO_KERNEL_CLUSTER(k) (k = 1, 2, 4 or 8) fixes the
+ * cluster size instead of the built-in cost model's choice. */
+#define DECO_KERNEL_CLUSTER(k) ((k) << 8)
+/* With DECO_KERNEL_ONCHIP, fixes the CTA size of the on-chip kernel. */
+#define DECO_KERNEL_THREADS_512 (1 << 12)
+#define DECO_KERNEL_THREADS_1024 (2 << 12)
+/* With DECO_KERNEL_ONCHIP and a cluster of more than one CTA, fixes how the
+ * CTAs exchange their new rows after every step: through distributed shared
+ * memory stores, or through L2 (global stores + one bulk copy per CTA). */
+#define DECO_KERNEL_EXCHANGE_DSMEM (1 << 14)
+#define DECO_KERNEL_EXCHANGE_L2 (2 << 14)
+
+/* deco_create_graph flags */
+#define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */
+
+typedef struct deco_graph deco_graph;
+
+/* Create a graph from a symmetric CSR (both orientations stored).
+ * Def. 1 / Eq. 1 of the paper (undirected graph, cut counts each crossing
+ * edge once); Sec. 2 notation for A, D, L.
+ *  n        >= 1 nodes; nnz >= 0 stored entries (= 2 m), nnz < 2^31.
+ *  row_ptr  host, n+1 int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *  col_idx  host, nnz int32 in [0,n), strictly increasing within each row,
+ *           no self loops; (u,v) present iff (v,u) present.
+ *  weights  host, nnz floats or NULL (unit weights).  Every weight must be a
+ *           nonzero integer with |w| <= 2^20 and w(u,v) = w(v,u) (cut values
+ *           are computed exactly in integers).
+ *  flags    DECO_GRAPH_* bits.
+ *  out      receives the handle; the library copies everything it needs to
+ *           the current device (the caller's arrays may be freed afterwards).
+ * Errors: DECO_ERR_ARG (NULL/size), DECO_ERR_GRAPH (validation; message says
+ * which rule and where), DECO_ERR_UNSUPPORTED (non-integral weights),
+ * DECO_ERR_OOM / DECO_ERR_CUDA.  Validation happens before any CUDA call. */
+int deco_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                      const float* weights, uint32_t flags, deco_graph** out);
+
+/* Release a graph (NULL is a no-op). */
+void deco_destroy_graph(deco_graph* g);
+
+/* Graph facts: n, nnz, and whether weights are present (1) or unit (0). */
+int deco_graph_info(const deco_graph* g, int32_t* n, int64_t* nnz, int32_t* weighted);
+
+/* Integer cut value of one binary vector (Def. 1, Eq. 1):
+ *   Cut = sum over unordered edges {u,v} with z_u != z_v of w_uv.
+ *  z        host, n bytes, each 0 or 1 (any nonzero byte counts as 1).
+ *  cut_out  host, receives the exact value.
+ * Synchronous.  Errors: DECO_ERR_ARG, DECO_ERR_OOM, DECO_ERR_CUDA. */
+int deco_eval_cut(const deco_graph* g, const uint8_t* z, int64_t* cut_out);
+
+/* Batched integer cut values (Eq. 1) of B binary columns.
+ *  z     device, n x B bytes row-major (z[v*B + b]), 0/1.
+ *  cuts  device, B int64 (overwritten).  Stream-ordered, asynchronous. */
+int deco_eval_cuts(const deco_graph* g, int32_t B, const uint8_t* z, int64_t* cuts, void* stream);
+
+/* Arguments of one fused PGA step.  Reading of the momentum form (the paper
+ * only says momentum PGA is used, Sec. 4.2): heavy ball,
+ *   V <- mu V + grad;  y <- Proj(y + alpha_eff V),
+ * with grad = d (.) y - A y (Laplacian, alpha_eff = alpha) or grad = -A y
+ * (multilinear, alpha_eff = 2 alpha). */
+typedef struct deco_step_args {
+  int32_t objective;          /* DECO_OBJ_* */
+  int32_t precision;          /* DECO_PREC_* of y_in / y_out */
+  float alpha;                /* step size when alpha_cols == NULL */
+  float momentum;             /* mu; 0 = plain PGA (v ignored, may be NULL) */
+  const float* alpha_cols;    /* device, C floats or NULL: per-column step size */
+  const int32_t* steps_cols;  /* device, C int32 or NULL: column c is active
+                                 only while t < steps_cols[c] (population search) */
+  int32_t t;                  /* step index used with steps_cols */
+  int32_t reserved;
+} deco_step_args;
+
+/* One projected gradient ascent step on every column (Eq. 7; Eq. 10 when the
+ * block is lifted -- each column updates independently, remark after Eq. 11).
+ *  C       columns, 1 <= C <= ld; ld % 8 == 0.
+ *  y_in    device, n x ld, precision a->precision; not modified.
+ *  y_out   device, n x ld, must not alias y_in; columns >= C untouched.
+ *  v       device, n x ld float (momentum buffer, FP32 always), updated in
+ *          place; may be NULL when a->momentum == 0.
+ *  nonfinite_flag  device int32 or NULL: set to 1 if any new value is not
+ *          finite (the value written is then clamped; the caller decides).
+ * Stream-ordered, asynchronous.  Errors: DECO_ERR_ARG. */
+int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void* y_out,
+              float* v, const deco_step_args* a, int32_t* nonfinite_flag, void* stream);
+
+/* `steps` projected gradient ascent steps in place (Alg. 1 / Alg. 2 lines
+ * 2-3): y holds the starting block and receives the result.
+ *  C, ld   as in deco_step; the on-chip kernel needs ld % 32 == 0 (FP32) or
+ *          ld % 64 == 0 (BF16) and treats columns in [C, ld) as inactive.
+ *  v       device n x ld float momentum, read at the start and written at the
+ *          end (NULL when a->momentum == 0).
+ *  a       step arguments; a->t is ignored (step t runs t = 0 .. steps-1).
+ *  kernel  DECO_KERNEL_* (with the optional ONCHIP modifiers above).
+ *  nonfinite_flag  device int32 or NULL: bit 0 set if a new value is not
+ *          finite; bit 1 set if a bounded wait of the on-chip kernel gave up
+ *          (the block is then unreliable).
+ * Stream-ordered and asynchronous; scratch memory (exchange buffers, the
+ * second block of the global kernel) is allocated and released in stream
+ * order.  The first use of a graph with a given cluster size builds its
+ * on-chip CSR image on the host (kept with the graph).
+ * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED (ONCHIP does not fit), CUDA. */
+int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
+                   const deco_step_args* a, int32_t kernel, int32_t* nonfinite_flag, void* stream);
+
+/* Rounding + cut + argmax of a block (Alg. 1/2 lines 4-6).
+ *  B, lift  starting points and lift l (C = B*l columns in y, ld >= C).
+ *  y        device, n x ld, precision `precision`.
+ *  zbits    device, n x ceil(B/32) uint32 (bit b%32 of word b/32 = z_{v,b}):
+ *           lift 1: z = 1{y > 0} (Eq. 5); lift l: z = 1{sum_i y_{v,bl+i} >= 0}
+ *           (Eq. 11, summed in FP32 in order i = 0..l-1).
+ *  cuts     device, B int64: cut of every starting point (Eq. 1).
+ *  best     device, 1 int32: lowest index among the maximal cuts, or NULL.
+ * Stream-ordered, asynchronous. */
+int deco_round_cut(const deco_graph* g, int32_t B, int32_t lift, int32_t ld, int32_t precision,
+                   const void* y, uint32_t* zbits, int64_t* cuts, int32_t* best, void* stream);
+
+/* Starting block of phase `phase` (Sec. 4.1, 4.2, 5).
+ *  init     DECO_INIT_*; for phases > 0 use DECO_INIT_MEAN with the previous
+ *           best vector mapped to 2z-1.
+ *  mean     device, n floats (DECO_INIT_MEAN) or NULL.
+ *  x0       device, n x ld floats (DECO_INIT_EXPLICIT) or NULL.
+ *  y        device, n x ld output block in `precision`.
+ * Random draws: Philox4x32-10 with key = seed and counter
+ * (row, column, phase, stream); see DESIGN notes in the source. */
+typedef struct deco_params {
+  int32_t objective;          /* DECO_OBJ_* */
+  int32_t precision;          /* DECO_PREC_* storage of the iterate */
+  int32_t init;               /* DECO_INIT_* of the first phase */
+  int32_t polish_steps;       /* BF16 only: last k steps of every phase in FP32 */
+  float eta;                  /* exploration variance (paper: 0.8) */
+  float scale;                /* down-scaling of Gaussian starts (paper: 1e-4) */
+  float beta;                 /* IDI threshold (paper: 0.2) */
+  float uniform_half_width;   /* DECO_INIT_UNIFORM half width (1 = full box) */
+  int32_t kernel;             /* DECO_KERNEL_* */
+  int32_t reserved;
+} deco_params;
+
+int deco_init_block(const deco_graph* g, int32_t B, int32_t lift, int32_t ld,
+                    const deco_params* p, uint64_t seed, int32_t phase,
+                    const float* mean, const float* x0, void* y, void* stream);
+
+/* IDI mean h_IDI in {-1,+1}^n (Sec. 4.1.2) into device h (n floats). */
+int deco_idi_mean(const deco_graph* g, float beta, uint64_t seed, int32_t phase, float* h,
+                  void* stream);
+
+/* DUI mean h_DUI (Eq. 12) into device h (n floats). */
+int deco_dui_mean(const deco_graph* g, uint64_t seed, int32_t phase, float* h, void* stream);
+
+/* One phase of Alg. 3: lift l = 1 (pQUCO, Alg. 1) or l >= 2 (pLUCO, Alg. 2). */
+typedef struct deco_phase {
+  int32_t lift;
+  int32_t steps;
+  float alpha;
+  float momentum;
+} deco_phase;
+
+typedef struct deco_result {
+  int64_t best_cut;       /* best cut over all phases (Alg. 1-3 return value) */
+  int32_t best_init;      /* starting point that produced it */
+  int32_t best_phase;     /* phase that produced it (earliest on ties) */
+  int64_t edge_updates;   /* sum over phases of nnz * B * l * steps */
+  double device_ms;       /* device time of the whole solve (CUDA events) */
+  int64_t kernel_launches;/* CUDA kernels this solve launched */
+} deco_result;
+
+/* pDECO (Alg. 3) over an explicit phase schedule; a one-phase schedule is
+ * pQUCO (Alg. 1) or pLUCO (Alg. 2).
+ *  B           starting points (>= 1).
+ *  phases      host, n_phases entries (1 <= n_phases <= 64).
+ *  p           host parameters.
+ *  x0          DECO_INIT_EXPLICIT: n x (B*lift0) floats, host or device;
+ *              otherwise NULL.
+ *  mean        DECO_INIT_MEAN: n floats, host or device; otherwise NULL.
+ *  assignment  host, n bytes or NULL: best binary vector (z_v = 1 -> v in S).
+ *  phase_cuts  host, n_phases x B int64 or NULL: every starting point's cut
+ *              after every phase.
+ *  out         host result.
+ * Synchronous (one stream sync at the end).  Scratch memory is allocated on
+ * the device for the call and released before returning.
+ * Errors: DECO_ERR_ARG, DECO_ERR_OOM, DECO_ERR_CUDA, DECO_ERR_NONFINITE. */
+int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t n_phases,
+               const deco_params* p, uint64_t seed, const float* x0, const float* mean,
+               uint8_t* assignment, int64_t* phase_cuts, void* stream, deco_result* out);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* deco_last_error(void);
+
+/* ABI version (DECO_ABI_VERSION) of the loaded library. */
+int deco_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECO_H_ */

@@ -1,0 +1,288 @@
+"""ctypes binding of libdeco.so (include/deco.h).
+
+Argument marshalling only: every computation of the hot path runs in the CUDA
+kernels behind the C ABI.  Device buffers are passed as torch CUDA tensors
+(their data pointers), host buffers as NumPy arrays, streams as
+torch.cuda.Stream objects or raw cudaStream_t integers.  There is no CPU
+fallback: if libdeco.so cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdeco.so")
+
+DECO_OK = 0
+DECO_ERR_ARG = -1
+DECO_ERR_GRAPH = -2
+DECO_ERR_OOM = -3
+DECO_ERR_CUDA = -4
+DECO_ERR_NONFINITE = -5
+DECO_ERR_TIMEOUT = -6
+DECO_ERR_UNSUPPORTED = -7
+STATUS_NAMES = {0: "DECO_OK", -1: "DECO_ERR_ARG", -2: "DECO_ERR_GRAPH", -3: "DECO_ERR_OOM",
+                -4: "DECO_ERR_CUDA", -5: "DECO_ERR_NONFINITE", -6: "DECO_ERR_TIMEOUT",
+                -7: "DECO_ERR_UNSUPPORTED"}
+
+DECO_OBJ_MULTILINEAR01 = 0
+DECO_OBJ_LAPLACIAN = 1
+DECO_PREC_FP32 = 0
+DECO_PREC_BF16 = 1
+DECO_INIT_UNIFORM = 0
+DECO_INIT_IDI = 1
+DECO_INIT_DUI = 2
+DECO_INIT_IDI_HALF_UNIFORM = 3
+DECO_INIT_EXPLICIT = 4
+DECO_INIT_MEAN = 5
+DECO_GRAPH_SKIP_SYMMETRY_CHECK = 0x1
+DECO_KERNEL_AUTO = 0
+DECO_KERNEL_GLOBAL = 1
+DECO_KERNEL_ONCHIP = 2
+
+# every function include/deco.h declares (checked by the CPU test-suite)
+EXPORTED = [
+    "deco_create_graph", "deco_destroy_graph", "deco_graph_info", "deco_eval_cut",
+    "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_round_cut", "deco_init_block",
+    "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
+]
+
+
+class DecoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class deco_step_args(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("momentum", ctypes.c_float),
+                ("alpha_cols", ctypes.c_void_p), ("steps_cols", ctypes.c_void_p),
+                ("t", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class deco_params(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("init", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
+                ("eta", ctypes.c_float), ("scale", ctypes.c_float), ("beta", ctypes.c_float),
+                ("uniform_half_width", ctypes.c_float), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class deco_phase(ctypes.Structure):
+    _fields_ = [("lift", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("momentum", ctypes.c_float)]
+
+
+class deco_result(ctypes.Structure):
+    _fields_ = [("best_cut", ctypes.c_int64), ("best_init", ctypes.c_int32),
+                ("best_phase", ctypes.c_int32), ("edge_updates", ctypes.c_int64),
+                ("device_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdeco.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I32, I64, U32, U64, F32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float
+    sig = {
+        "deco_create_graph": (ctypes.c_int, [I32, I64, P, P, P, U32, ctypes.POINTER(P)]),
+        "deco_destroy_graph": (None, [P]),
+        "deco_graph_info": (ctypes.c_int, [P, P, P, P]),
+        "deco_eval_cut": (ctypes.c_int, [P, P, P]),
+        "deco_eval_cuts": (ctypes.c_int, [P, I32, P, P, P]),
+        "deco_step": (ctypes.c_int, [P, I32, I32, P, P, P, ctypes.POINTER(deco_step_args), P, P]),
+        "deco_run_phase": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), I32, P, P]),
+        "deco_round_cut": (ctypes.c_int, [P, I32, I32, I32, I32, P, P, P, P, P]),
+        "deco_init_block": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(deco_params), U64, I32, P, P, P, P]),
+        "deco_idi_mean": (ctypes.c_int, [P, F32, U64, I32, P, P]),
+        "deco_dui_mean": (ctypes.c_int, [P, U64, I32, P, P]),
+        "deco_solve": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_phase), I32, ctypes.POINTER(deco_params),
+                                      U64, P, P, P, P, P, ctypes.POINTER(deco_result)]),
+        "deco_last_error": (ctypes.c_char_p, []),
+        "deco_abi_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.deco_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != DECO_OK:
+        raise DecoError(rc, last_error())
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a torch tensor / NumPy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class Graph:
+    """Owning handle of a deco_graph (destroyed with the object)."""
+
+    def __init__(self, handle: int, n: int, nnz: int):
+        self.handle = handle
+        self.n = n
+        self.nnz = nnz
+
+    def close(self):
+        if self.handle:
+            lib.deco_destroy_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+
+def deco_create_graph(n: int, row_ptr, col_idx, weights=None, flags: int = 0) -> Graph:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    h = ctypes.c_void_p()
+    nnz = ci.size
+    _check(lib.deco_create_graph(int(n), int(nnz), _ptr(rp), _ptr(ci) if ci.size else None,
+                                 _ptr(w), int(flags), ctypes.byref(h)))
+    return Graph(h.value, int(n), int(nnz))
+
+
+def graph_from(g, flags: int = 0) -> Graph:
+    """deco_create_graph from a graphgen.Graph-like object (n, row_ptr, col_idx, weights)."""
+    return deco_create_graph(g.n, g.row_ptr, g.col_idx, g.weights, flags)
+
+
+def deco_destroy_graph(g: Graph):
+    g.close()
+
+
+def deco_graph_info(g: Graph):
+    n, nnz, wt = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib.deco_graph_info(g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(wt)))
+    return n.value, nnz.value, wt.value
+
+
+def deco_eval_cut(g: Graph, z) -> int:
+    zz = np.ascontiguousarray(z, dtype=np.uint8)
+    if zz.size != g.n:
+        raise ValueError("z must have n entries")
+    out = ctypes.c_int64()
+    _check(lib.deco_eval_cut(g, _ptr(zz), ctypes.byref(out)))
+    return out.value
+
+
+def deco_eval_cuts(g: Graph, B: int, z_dev, cuts_dev, stream=None):
+    _check(lib.deco_eval_cuts(g, int(B), _ptr(z_dev), _ptr(cuts_dev), _stream(stream)))
+
+
+def step_args(objective=DECO_OBJ_MULTILINEAR01, precision=DECO_PREC_FP32, alpha=0.01, momentum=0.0,
+              alpha_cols=None, steps_cols=None, t=0) -> deco_step_args:
+    return deco_step_args(objective, precision, alpha, momentum, _ptr(alpha_cols), _ptr(steps_cols), t, 0)
+
+
+def deco_step(g: Graph, C: int, ld: int, y_in, y_out, v, args: deco_step_args, flag=None, stream=None):
+    _check(lib.deco_step(g, int(C), int(ld), _ptr(y_in), _ptr(y_out), _ptr(v), ctypes.byref(args),
+                         _ptr(flag), _stream(stream)))
+
+
+def deco_run_phase(g: Graph, C: int, ld: int, y, v, steps: int, args: deco_step_args,
+                   kernel: int = DECO_KERNEL_AUTO, flag=None, stream=None):
+    _check(lib.deco_run_phase(g, int(C), int(ld), _ptr(y), _ptr(v), int(steps), ctypes.byref(args),
+                              int(kernel), _ptr(flag), _stream(stream)))
+
+
+def deco_round_cut(g: Graph, B: int, lift: int, ld: int, precision: int, y, zbits, cuts, best=None,
+                   stream=None):
+    _check(lib.deco_round_cut(g, int(B), int(lift), int(ld), int(precision), _ptr(y), _ptr(zbits),
+                              _ptr(cuts), _ptr(best), _stream(stream)))
+
+
+def params(objective=DECO_OBJ_MULTILINEAR01, precision=DECO_PREC_FP32, init=DECO_INIT_UNIFORM,
+           polish_steps=0, eta=0.8, scale=1e-4, beta=0.2, uniform_half_width=1.0,
+           kernel=DECO_KERNEL_AUTO) -> deco_params:
+    return deco_params(objective, precision, init, polish_steps, eta, scale, beta, uniform_half_width,
+                       kernel, 0)
+
+
+def deco_init_block(g: Graph, B: int, lift: int, ld: int, p: deco_params, seed: int, phase: int, y,
+                    mean=None, x0=None, stream=None):
+    _check(lib.deco_init_block(g, int(B), int(lift), int(ld), ctypes.byref(p), int(seed), int(phase),
+                               _ptr(mean), _ptr(x0), _ptr(y), _stream(stream)))
+
+
+def deco_idi_mean(g: Graph, beta: float, seed: int, phase: int, h, stream=None):
+    _check(lib.deco_idi_mean(g, float(beta), int(seed), int(phase), _ptr(h), _stream(stream)))
+
+
+def deco_dui_mean(g: Graph, seed: int, phase: int, h, stream=None):
+    _check(lib.deco_dui_mean(g, int(seed), int(phase), _ptr(h), _stream(stream)))
+
+
+def deco_solve(g: Graph, B: int, phases: Sequence, p: deco_params, seed: int, x0=None, mean=None,
+               want_assignment: bool = True, want_phase_cuts: bool = True, stream=None):
+    """pDECO over `phases` (sequence of (lift, steps, alpha, momentum)).
+
+    Returns (deco_result, assignment uint8[n] or None, phase_cuts int64[n_phases, B] or None).
+    """
+    arr = (deco_phase * len(phases))(*[deco_phase(int(l), int(s), float(a), float(m)) for l, s, a, m in phases])
+    assignment = np.zeros(g.n, dtype=np.uint8) if want_assignment else None
+    pc = np.zeros((len(phases), B), dtype=np.int64) if want_phase_cuts else None
+    x0p = x0
+    if isinstance(x0, np.ndarray):
+        x0p = np.ascontiguousarray(x0, dtype=np.float32)
+    meanp = mean
+    if isinstance(mean, np.ndarray):
+        meanp = np.ascontiguousarray(mean, dtype=np.float32)
+    res = deco_result()
+    _check(lib.deco_solve(g, int(B), arr, len(phases), ctypes.byref(p), int(seed), _ptr(x0p), _ptr(meanp),
+                          _ptr(assignment), _ptr(pc), _stream(stream), ctypes.byref(res)))
+    return res, assignment, pc
+
+
+def deco_abi_version() -> int:
+    return lib.deco_abi_version()

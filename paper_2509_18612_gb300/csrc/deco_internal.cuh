@@ -1,0 +1,174 @@
+// Internal declarations shared by the translation units of libdeco.
+// Device helpers (counter-based RNG, bf16 packing), the graph handle and the
+// kernel launchers.  Nothing here is part of the public ABI (include/deco.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "deco.h"
+
+namespace deco {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char* what);   // records message, returns DECO_ERR_CUDA / OOM
+
+#define DECO_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::deco::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Weight storage of a graph.
+enum WeightMode : int {
+  W_UNIT = 0,     // all weights 1: no weight array
+  W_SIGN = 1,     // weights in {-1,+1}: sign stored in bit 31 of the column index
+  W_GENERAL = 2   // integral weights in a float array
+};
+
+}  // namespace deco
+
+// Shared-memory CSR image of a row split of a graph for the on-chip kernel
+// (built once per cluster size and kept with the graph).
+struct SlabImage {
+  int k = 0;
+  uint32_t* data = nullptr;          // device, all parts back to back
+  int32_t off[9] = {0};              // part i at data + 4 * off[i] (16-byte units)
+  int32_t split[9] = {0};            // row split
+  int32_t max_own = 0;
+  int32_t max_words = 0;             // largest part in 32-bit words
+};
+
+// The opaque handle of the ABI.
+struct deco_graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int weighted = 0;             // caller supplied weights
+  int wmode = deco::W_UNIT;     // storage used by the kernels
+  int device = 0;
+  // host-side facts (degree statistics for IDI / DUI)
+  int64_t deg_s1 = 0, deg_s2 = 0;
+  int32_t max_deg = 0;
+  std::vector<int32_t> h_row_ptr;   // host copy (row splits of the on-chip kernel)
+  std::vector<int32_t> h_col;       // host copy of the device edge order
+  std::vector<float> h_w;           // host copy of the device-order weights (or empty)
+  std::vector<SlabImage> images;    // on-chip CSR images, one per cluster size used
+  // device arrays
+  int32_t* row_ptr = nullptr;   // n+1
+  int32_t* col_idx = nullptr;   // nnz, plain indices
+  uint32_t* col_sw = nullptr;   // nnz, index | sign bit (W_SIGN only)
+  float* w = nullptr;           // nnz (W_GENERAL only)
+  int32_t* wint = nullptr;      // nnz integer weights (weighted graphs; cut evaluation)
+  float* dnet = nullptr;        // n, net weighted degree d_v = sum_u w_vu
+  int32_t* deg = nullptr;       // n, |N(v)|
+};
+
+namespace deco {
+
+// ------------------------------------------------------------- device helpers
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies, key advanced by
+// the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+    uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform in (0,1): (2*(x>>9)+1) * 2^-24, exact in FP32.
+__device__ __forceinline__ float u01(uint32_t x) {
+  return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+
+// Standard normal by the Box-Muller transform of two uniforms.
+__device__ __forceinline__ float box_muller(uint32_t a, uint32_t b) {
+  float r = sqrtf(-2.0f * logf(u01(a)));
+  return r * cospif(2.0f * u01(b));
+}
+
+enum RngStream : uint32_t { STREAM_INIT = 0, STREAM_IDI = 1, STREAM_DUI = 2, STREAM_EVOLVE = 3 };
+
+// bf16 <-> fp32 packing of a 32-bit word holding two bf16 values (low half first).
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------- launchers
+
+struct StepLaunch {
+  int32_t n, C, ld;
+  int precision, objective, wmode;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const uint32_t* col_sw;
+  const float* w;
+  const float* dnet;
+  const void* yin;
+  void* yout;
+  float* v;
+  float alpha;          // step size (before the objective's factor)
+  float mu;
+  const float* alpha_cols;
+  const int32_t* steps_cols;
+  int32_t t;
+  int32_t* flag;
+};
+int launch_step_global(const StepLaunch& s, cudaStream_t st);
+
+int launch_pack(const deco_graph* g, int32_t B, int32_t lift, int32_t ld, int precision,
+                const void* y, uint32_t* zbits, cudaStream_t st);
+int launch_cut_bits(const deco_graph* g, int32_t B, const uint32_t* zbits, int64_t* cuts,
+                    cudaStream_t st);
+int launch_cut_bytes(const deco_graph* g, int32_t B, const uint8_t* z, int64_t* cuts,
+                     cudaStream_t st);
+int launch_argmax(int32_t B, const int64_t* cuts, int32_t* best, cudaStream_t st);
+
+// Phase bookkeeping of deco_solve: best of the phase, global best record.
+struct BestRecord {
+  long long cut;
+  int32_t init;
+  int32_t phase;
+  int32_t improved;   // last phase improved the record
+  int32_t pad;
+};
+int launch_phase_finish(const deco_graph* g, int32_t B, int32_t phase, const int64_t* cuts,
+                        const uint32_t* zbits, int32_t* best_idx, BestRecord* rec,
+                        uint8_t* phase_best_z, uint8_t* best_z, cudaStream_t st);
+
+struct InitLaunch {
+  int32_t n, B, lift, ld;
+  int precision, objective, init;
+  float eta, scale, uniform_half_width;
+  uint32_t k0, k1;
+  int32_t phase;
+  const float* mean;          // n floats (Gaussian modes)
+  const uint8_t* mean_bits;   // n bytes z* (mean = 2z-1) instead of `mean`
+  const float* x0;            // explicit start (ld stride)
+  void* y;
+};
+int launch_init(const InitLaunch& p, cudaStream_t st);
+int launch_idi(const deco_graph* g, double thresh, uint32_t k0, uint32_t k1, int32_t phase,
+               float* h, int8_t* side_scratch, cudaStream_t st);
+int launch_dui(const deco_graph* g, uint32_t k0, uint32_t k1, int32_t phase, float* h,
+               cudaStream_t st);
+
+double idi_threshold(const deco_graph* g, float beta);
+
+}  // namespace deco

@@ -1,0 +1,204 @@
+// One phase of projected gradient ascent (Alg. 1 / Alg. 2 lines 2-3): T steps
+// on a device block, by the persistent on-chip kernel (slab.cu) when one
+// column slab of the graph fits in shared memory, otherwise by one launch of
+// the global-memory kernel (step_global.cu) per step.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "deco_internal.cuh"
+#include "phase.cuh"
+#include "slab.cuh"
+
+namespace deco {
+
+int device_sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+  }
+  return sms;
+}
+
+// Exact sizes of the on-chip CSR image of a split (see slab.cuh).
+static void image_sizes(const deco_graph* g, int k, const int32_t* split, int32_t* max_own,
+                        int64_t* max_words, int64_t* max_edges) {
+  *max_own = 0;
+  *max_words = 0;
+  *max_edges = 0;
+  const bool gen = g->wmode == W_GENERAL;
+  for (int part = 0; part < k; ++part) {
+    const int r0 = split[part], r1 = split[part + 1];
+    int64_t E = 0;
+    for (int r = r0; r < r1; ++r) {
+      const int e0 = g->h_row_ptr[r], e1 = g->h_row_ptr[r + 1];
+      int nn = 0;
+      if (g->wmode == W_SIGN)
+        for (int e = e0; e < e1; ++e) nn += g->h_w[e] < 0.0f;
+      const int np = (e1 - e0) - nn;
+      E += (np + 3) / 4 * 4 + (nn + 3) / 4 * 4;
+    }
+    E += 8;
+    int64_t words = 4 * (int64_t)(r1 - r0 + 1) + E * (gen ? 2 : 1);
+    words = (words + 3) / 4 * 4;
+    *max_own = std::max(*max_own, r1 - r0);
+    *max_words = std::max(*max_words, words);
+    *max_edges = std::max<int64_t>(*max_edges, g->h_row_ptr[r1] - g->h_row_ptr[r0]);
+  }
+}
+
+// Cost model of one step of the on-chip kernel, in units of one 128-byte
+// shared-memory row read: own gathers + broadcast of the staged rows (all n
+// rows land in every replica when k > 1) + epilogue + barrier latency.
+static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int waves) {
+  const double per_cta = 1.25 * (double)own_nnz + (k > 1 ? (double)n : (double)own) + 4.0 * own + 1500.0;
+  return per_cta * waves;
+}
+
+int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, PhasePlan* plan) {
+  *plan = PhasePlan{};
+  plan->kernel = KERNEL_GLOBAL;
+  const int cols = prec == DECO_PREC_BF16 ? 64 : 32;
+  const int want_k = (force >> 8) & 0xF;
+  const int want_t = (force >> 12) & 0x3;
+  const int want_x = (force >> 14) & 0x3;
+  force &= 0xFF;
+  plan->threads = want_t == 1 ? 512 : 1024;
+  plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
+  if (force == DECO_KERNEL_GLOBAL) return DECO_OK;
+  const bool aligned = ld % cols == 0;
+  const int max_smem = slab_max_smem();
+  const int items = (C + cols - 1) / cols;
+  const int sms = device_sm_count();
+  double best = 0.0;
+  // the replica alone must fit before any split is worth sizing
+  const bool replica_fits = (size_t)g->n * 128 + 4096 <= (size_t)max_smem;
+  for (int k = 1; k <= SLAB_MAX_CLUSTER && aligned && replica_fits; k *= 2) {
+    if (k > g->n) break;
+    if (want_k && k != want_k) continue;
+    int32_t split[SLAB_MAX_CLUSTER + 1];
+    slab_split(g->h_row_ptr.data(), g->n, k, split);
+    int32_t max_own = 0;
+    int64_t max_words = 0, max_edges = 0;
+    image_sizes(g, k, split, &max_own, &max_words, &max_edges);
+    if (max_words > (1 << 26)) continue;
+    const size_t smem = slab_smem_bytes(g->n, max_own, (int)max_words, prec);
+    if (smem > (size_t)max_smem) continue;
+    const int per_sm = std::max(1, std::min(4, (int)((size_t)(max_smem + 1024) / (smem + 1024))));
+    const int waves = (int)((items * (int64_t)k + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm));
+    const double cost = onchip_cost(max_edges, max_own, g->n, k, waves);
+    if (plan->kernel != KERNEL_ONCHIP || cost < best) {
+      best = cost;
+      plan->kernel = KERNEL_ONCHIP;
+      plan->k = k;
+      plan->max_own = max_own;
+      plan->max_img_words = (int32_t)max_words;
+      plan->items = items;
+    }
+  }
+  if (force == DECO_KERNEL_ONCHIP && plan->kernel != KERNEL_ONCHIP) {
+    set_error("the on-chip kernel does not fit this graph (n=%d, nnz=%lld, ld=%d)", g->n,
+              (long long)g->nnz, ld);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  return DECO_OK;
+}
+
+static std::mutex g_image_mutex;
+
+int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec_, int force,
+                         cudaStream_t st) {
+  (void)st;
+  g = g_;
+  C = C_;
+  ld = ld_;
+  prec = prec_;
+  int rc = plan_phase(g, C, ld, prec, force, &plan);
+  if (rc) return rc;
+  if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_image_mutex);
+    // the image cache lives with the graph; building it does not change the
+    // graph's meaning, only how the on-chip kernel reads it
+    const SlabImage* im = nullptr;
+    rc = slab_image(const_cast<deco_graph*>(g), plan.k, &im);
+    if (rc) return rc;
+    plan.image = *im;
+  }
+  if (plan.k > 1 && plan.xmode == 2) {
+    const size_t bytes = 2 * (size_t)plan.items * g->n * 128;
+    cudaError_t e = cudaMallocAsync((void**)&xbuf, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(exchange buffer)");
+  }
+  return DECO_OK;
+}
+
+int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objective, float alpha, float mu,
+                     const float* alpha_cols, const int32_t* steps_cols, bool load_v, bool store_v,
+                     int32_t* flag, cudaStream_t st, int64_t* kernels) {
+  if (plan.kernel == KERNEL_ONCHIP) {
+    SlabParams p{};
+    SlabGraph& sg = p.g0;
+    sg.n = g->n; sg.ld = ld; sg.C = C;
+    sg.dnet = g->dnet;
+    sg.image = reinterpret_cast<const uint4*>(plan.image.data);
+    std::copy(plan.image.off, plan.image.off + SLAB_MAX_CLUSTER + 1, sg.img_off);
+    std::copy(plan.image.split, plan.image.split + SLAB_MAX_CLUSTER + 1, sg.split);
+    sg.y = y[cur];
+    sg.v = v;
+    sg.alpha_cols = alpha_cols;
+    sg.steps_cols = steps_cols;
+    sg.xbuf = xbuf;
+    sg.nslabs = plan.items;
+    p.graphs = nullptr;
+    p.items = nullptr;
+    p.k = plan.k;
+    p.threads = plan.threads;
+    p.xmode = plan.xmode;
+    p.steps = steps;
+    const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
+    p.alpha = fac * alpha;
+    p.afac = fac;
+    p.mu = mu;
+    p.objective = objective;
+    p.load_v = load_v ? 1 : 0;
+    p.store_v = store_v ? 1 : 0;
+    p.max_n = g->n;
+    p.max_own = plan.image.max_own;
+    p.max_img_words = plan.image.max_words;
+    p.flag = flag;
+    int rc = launch_slab(p, plan.items, prec, g->wmode, st);
+    if (rc) return rc;
+    if (kernels) *kernels += 1;
+    return DECO_OK;
+  }
+  StepLaunch sl{};
+  sl.n = g->n; sl.C = C; sl.ld = ld;
+  sl.precision = prec; sl.objective = objective; sl.wmode = g->wmode;
+  sl.row_ptr = g->row_ptr; sl.col_idx = g->col_idx; sl.col_sw = g->col_sw; sl.w = g->w;
+  sl.dnet = g->dnet;
+  sl.v = v; sl.alpha = alpha; sl.mu = mu;
+  sl.alpha_cols = alpha_cols; sl.steps_cols = steps_cols; sl.flag = flag;
+  for (int32_t t = 0; t < steps; ++t) {
+    sl.yin = y[cur];
+    sl.yout = y[cur ^ 1];
+    sl.t = t;
+    int rc = launch_step_global(sl, st);
+    if (rc) return rc;
+    cur ^= 1;
+  }
+  if (kernels) *kernels += steps;
+  return DECO_OK;
+}
+
+void PhaseRunner::release(cudaStream_t st) {
+  if (xbuf) cudaFreeAsync(xbuf, st);
+  xbuf = nullptr;
+}
+
+}  // namespace deco

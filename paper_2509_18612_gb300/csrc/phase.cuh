@@ -1,0 +1,43 @@
+// Phase runner: choice between the on-chip persistent kernel and the
+// per-step global-memory kernel, and the launch of one phase.
+#pragma once
+
+#include "deco_internal.cuh"
+#include "slab.cuh"
+
+namespace deco {
+
+enum KernelKind { KERNEL_GLOBAL = 0, KERNEL_ONCHIP = 1 };
+
+struct PhasePlan {
+  int kernel = KERNEL_GLOBAL;
+  int k = 1;                     // cluster size of the on-chip kernel
+  int threads = 1024;            // CTA size of the on-chip kernel
+  int xmode = 2;                 // exchange between cluster CTAs: 1 DSMEM, 2 L2
+  int items = 0;                 // column slabs
+  int32_t max_own = 0, max_img_words = 0;
+  SlabImage image;               // on-chip CSR image (owned by the graph)
+};
+
+int device_sm_count();
+// force: DECO_KERNEL_* optionally | DECO_KERNEL_CLUSTER(k)
+int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, PhasePlan* plan);
+
+struct PhaseRunner {
+  const deco_graph* g = nullptr;
+  int32_t C = 0, ld = 0;
+  int prec = 0;
+  PhasePlan plan;
+  unsigned char* xbuf = nullptr;  // exchange buffer of the on-chip kernel (k > 1)
+
+  // choose the kernel for a C-column block of g (builds the CSR image once)
+  int prepare(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, cudaStream_t st);
+  // `steps` steps on y[cur] (the global kernel ping-pongs y[0] / y[1] and
+  // updates cur; the on-chip kernel works in place)
+  int run(void* y[2], int& cur, float* v, int32_t steps, int objective, float alpha, float mu,
+          const float* alpha_cols, const int32_t* steps_cols, bool load_v, bool store_v, int32_t* flag,
+          cudaStream_t st, int64_t* kernels);
+  void release(cudaStream_t st);
+};
+
+}  // namespace deco
