@@ -197,6 +197,27 @@ int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void
 int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
                    const deco_step_args* a, int32_t kernel, int32_t* nonfinite_flag, void* stream);
 
+/* deco_run_phase for callers that cannot let the library allocate device
+ * memory: a host program whose own pool already holds (nearly) all of the
+ * device, or a latency-bound loop where a cudaMalloc/cudaFree, which may
+ * synchronise the device, is not acceptable.  The paper has no counterpart;
+ * this is a deployment variant of the per-step phase runner above.
+ *  Same arguments as deco_run_phase, always on the per-step global-memory
+ *  kernel.  Results equal deco_run_phase with DECO_KERNEL_GLOBAL.
+ *  Scratch: the second block of the step ping-pong lives in one fixed
+ *  16 MiB device array inside the library (every GPU that loads the library
+ *  keeps it until the process exits); n * ld * element size must not exceed
+ *  16 MiB, otherwise DECO_ERR_UNSUPPORTED with a message, and nothing runs.
+ *  No cudaMalloc, cudaFree or other allocating call is made.
+ *  The first call on a device looks up the array's device address
+ *  (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  All calls share the one array: calls whose work overlaps on the GPU (other
+ *  streams, other host threads) race on it and must be serialised by the
+ *  caller.  Nothing in the array needs to start at zero.
+ * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED, DECO_ERR_CUDA. */
+int deco_run_phase_noalloc(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
+                           const deco_step_args* a, int32_t* nonfinite_flag, void* stream);
+
 /* Rounding + cut + argmax of a block (Alg. 1/2 lines 4-6).
  *  B, lift  starting points and lift l (C = B*l columns in y, ld >= C).
  *  y        device, n x ld, precision `precision`.

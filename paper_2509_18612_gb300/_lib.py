@@ -47,7 +47,8 @@ DECO_KERNEL_ONCHIP = 2
 # every function include/deco.h declares (checked by the CPU test-suite)
 EXPORTED = [
     "deco_create_graph", "deco_destroy_graph", "deco_graph_info", "deco_eval_cut",
-    "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_round_cut", "deco_init_block",
+    "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_run_phase_noalloc", "deco_round_cut",
+    "deco_init_block",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
 ]
 
@@ -98,6 +99,7 @@ def _load():
         "deco_eval_cuts": (ctypes.c_int, [P, I32, P, P, P]),
         "deco_step": (ctypes.c_int, [P, I32, I32, P, P, P, ctypes.POINTER(deco_step_args), P, P]),
         "deco_run_phase": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), I32, P, P]),
+        "deco_run_phase_noalloc": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), P, P]),
         "deco_round_cut": (ctypes.c_int, [P, I32, I32, I32, I32, P, P, P, P, P]),
         "deco_init_block": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(deco_params), U64, I32, P, P, P, P]),
         "deco_idi_mean": (ctypes.c_int, [P, F32, U64, I32, P, P]),
@@ -234,6 +236,16 @@ def deco_run_phase(g: Graph, C: int, ld: int, y, v, steps: int, args: deco_step_
                    kernel: int = DECO_KERNEL_AUTO, flag=None, stream=None):
     _check(lib.deco_run_phase(g, int(C), int(ld), _ptr(y), _ptr(v), int(steps), ctypes.byref(args),
                               int(kernel), _ptr(flag), _stream(stream)))
+
+
+def deco_run_phase_noalloc(g: Graph, C: int, ld: int, y, v, steps: int, args: deco_step_args, flag=None,
+                           stream=None):
+    """deco_run_phase for callers that cannot let the library allocate device
+    memory (their own pool holds the device, or allocation latency is not
+    acceptable): the step kernel's second block lives in a fixed 16 MiB array
+    inside the library.  Blocks larger than that are refused."""
+    _check(lib.deco_run_phase_noalloc(g, int(C), int(ld), _ptr(y), _ptr(v), int(steps), ctypes.byref(args),
+                                      _ptr(flag), _stream(stream)))
 
 
 def deco_round_cut(g: Graph, B: int, lift: int, ld: int, precision: int, y, zbits, cuts, best=None,
