@@ -109,8 +109,16 @@ def run_deco(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    from paper_2509_18612_gb300.tuning import TuningTable
     gs = graphs()
     handles = [deco.graph_from(g) for g in gs]
+    # untimed set-up: the autotuner picks the launch shape of every block shape
+    tt = TuningTable()
+    tuned = {}
+    for gname, G in zip(("er", "torus"), handles):
+        for C in (B, 2 * B):
+            for prec in (deco.DECO_PREC_FP32, deco.DECO_PREC_BF16):
+                tuned[f"{gname}/C{C}/{'bf16' if prec else 'fp32'}"] = hex(tt.ensure(G, C, prec))
     p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM,
                     precision=deco.DECO_PREC_BF16 if args.precision == "bf16" else deco.DECO_PREC_FP32,
                     polish_steps=args.polish if args.precision == "bf16" else 0)
@@ -163,6 +171,8 @@ def run_deco(args, rank, world):
         h2d = d2h = 0
         for g in gs:
             G = deco.graph_from(g)
+            for C in (B, 2 * B):
+                tt.ensure(G, C, p.precision)      # installs the recorded shape (no timing)
             res, z, pc = deco.deco_solve(G, B, SCHEDULE, p, 4242, stream=stream)
             G.close()
             h2d += g.row_ptr.nbytes + g.col_idx.nbytes + (0 if g.weights is None else g.nnz * 4)
@@ -197,7 +207,8 @@ def run_deco(args, rank, world):
         other = {"dtype": op, "value": edge_updates(gs) / (a.elapsed_time(b) / 1e3),
                  "polish_steps": args.polish if op == "bf16" else 0, "best_cuts": bc}
     return {"value": value, "ms": ms, "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
-            "best_cuts": cuts[-1], "gpu_launches": timed_launches, "other_precision": other}
+            "best_cuts": cuts[-1], "gpu_launches": timed_launches, "other_precision": other,
+            "tuned": tuned}
 
 
 ROOF_STEPS = 800
@@ -222,7 +233,7 @@ def roofline_step(args, deco, torch, dev, G, g):
     a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, prec, 0.01, 0.9)
     st = torch.cuda.current_stream()
     y = y0.clone()
-    deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_ONCHIP, None, st)
+    deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_AUTO, None, st)   # tuned shape
     reps = 5
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
@@ -230,7 +241,7 @@ def roofline_step(args, deco, torch, dev, G, g):
         y.copy_(y0)
         v.zero_()
         e0.record(st)
-        deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_ONCHIP, None, st)
+        deco.deco_run_phase(G, C, ld, y, v, ROOF_STEPS, a, deco.DECO_KERNEL_AUTO, None, st)
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -271,8 +282,34 @@ def run_reference(args, rank, world):
             "sample": f"per step: first phase only, {cols} of {B} starting points, {steps} of 2000 steps, both graphs"}
 
 
+def profile_kernel(sel: int, precision: str):
+    """Two launches of the dominant kernel (one 800-step unlifted phase of the
+    ER graph, C = 1024) with a fixed launch-shape selector, for ncu captures
+    (capture the second launch)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    g = graphs()[0]
+    G = deco.graph_from(g)
+    prec = deco.DECO_PREC_BF16 if precision == "bf16" else deco.DECO_PREC_FP32
+    dt = torch.bfloat16 if precision == "bf16" else torch.float32
+    y0 = (torch.rand(g.n, B, device="cuda") * 2e-4 - 1e-4).to(dt)
+    v = torch.zeros(g.n, B, device="cuda")
+    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, prec, 0.01, 0.9)
+    for i in range(2):
+        y = y0.clone()
+        v.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        deco.deco_run_phase(G, B, B, y, v, ROOF_STEPS, a, sel)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"launch": i, "selector": hex(sel), "us_per_step": e0.elapsed_time(e1) * 1e3 / ROOF_STEPS}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-kernel", type=lambda s: int(s, 0), default=None,
+                    help="run only the dominant kernel twice with this launch-shape selector")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -283,6 +320,9 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.profile_kernel is not None:
+        profile_kernel(args.profile_kernel, args.precision)
+        return
     if args.impl == "reference":
         if rank != 0:
             return
@@ -319,6 +359,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": r["clocks"], "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
                 "gpu_launches": r["gpu_launches"], "other_precision": r["other_precision"],
+                "tuned_kernels": r["tuned"],
                 "best_cuts": r["best_cuts"]}
         print(json.dumps(line))
     if world > 1:

@@ -197,6 +197,25 @@ int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void
 int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
                    const deco_step_args* a, int32_t kernel, int32_t* nonfinite_flag, void* stream);
 
+/* Autotuner: times every feasible launch shape of a phase on this graph --
+ * the per-step global kernel and the on-chip kernel for each cluster size
+ * (1, 2, 4, 8), CTA size (512, 1024) and exchange mode (DSMEM, L2) -- over
+ * `probe_steps` steps of a C-column block with the given precision,
+ * objective and momentum, and records the fastest with the graph.  Later
+ * deco_solve / deco_run_phase calls with DECO_KERNEL_AUTO on a block of the
+ * same C and precision use the recorded shape instead of the cost model.
+ *  best_kernel        host, receives the winning DECO_KERNEL_* selector.
+ *  best_us_per_step   host, receives its time per step (microseconds).
+ * Allocates and frees its own probe blocks; synchronous.
+ * Errors: DECO_ERR_ARG, DECO_ERR_OOM, DECO_ERR_CUDA. */
+int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, int32_t objective, float momentum,
+                  int32_t probe_steps, int32_t* best_kernel, float* best_us_per_step, void* stream);
+
+/* Record a launch shape for (C, precision) on this graph without timing it
+ * (e.g. one loaded from a saved tuning table); `kernel` must be a valid
+ * DECO_KERNEL_* selector.  Errors: DECO_ERR_ARG. */
+int deco_set_tuning(const deco_graph* g, int32_t C, int32_t precision, int32_t kernel);
+
 /* deco_run_phase for callers that cannot let the library allocate device
  * memory: a host program whose own pool already holds (nearly) all of the
  * device, or a latency-bound loop where a cudaMalloc/cudaFree, which may

@@ -48,7 +48,7 @@ DECO_KERNEL_ONCHIP = 2
 EXPORTED = [
     "deco_create_graph", "deco_destroy_graph", "deco_graph_info", "deco_eval_cut",
     "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_run_phase_noalloc", "deco_round_cut",
-    "deco_init_block",
+    "deco_init_block", "deco_autotune", "deco_set_tuning",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
 ]
 
@@ -100,6 +100,8 @@ def _load():
         "deco_step": (ctypes.c_int, [P, I32, I32, P, P, P, ctypes.POINTER(deco_step_args), P, P]),
         "deco_run_phase": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), I32, P, P]),
         "deco_run_phase_noalloc": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), P, P]),
+        "deco_autotune": (ctypes.c_int, [P, I32, I32, I32, F32, I32, P, P, P]),
+        "deco_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
         "deco_round_cut": (ctypes.c_int, [P, I32, I32, I32, I32, P, P, P, P, P]),
         "deco_init_block": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(deco_params), U64, I32, P, P, P, P]),
         "deco_idi_mean": (ctypes.c_int, [P, F32, U64, I32, P, P]),
@@ -246,6 +248,20 @@ def deco_run_phase_noalloc(g: Graph, C: int, ld: int, y, v, steps: int, args: de
     inside the library.  Blocks larger than that are refused."""
     _check(lib.deco_run_phase_noalloc(g, int(C), int(ld), _ptr(y), _ptr(v), int(steps), ctypes.byref(args),
                                       _ptr(flag), _stream(stream)))
+
+
+def deco_autotune(g: Graph, C: int, precision: int = DECO_PREC_FP32, objective: int = DECO_OBJ_MULTILINEAR01,
+                  momentum: float = 0.9, probe_steps: int = 50, stream=None):
+    """Time every launch shape of a C-column phase on g; returns (selector, us_per_step)."""
+    sel = ctypes.c_int32()
+    us = ctypes.c_float()
+    _check(lib.deco_autotune(g, int(C), int(precision), int(objective), float(momentum), int(probe_steps),
+                             ctypes.byref(sel), ctypes.byref(us), _stream(stream)))
+    return sel.value, us.value
+
+
+def deco_set_tuning(g: Graph, C: int, precision: int, kernel: int):
+    _check(lib.deco_set_tuning(g, int(C), int(precision), int(kernel)))
 
 
 def deco_round_cut(g: Graph, B: int, lift: int, ld: int, precision: int, y, zbits, cuts, best=None,

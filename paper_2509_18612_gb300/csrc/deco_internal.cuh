@@ -59,6 +59,10 @@ struct deco_graph {
   std::vector<int32_t> h_col;       // host copy of the device edge order
   std::vector<float> h_w;           // host copy of the device-order weights (or empty)
   std::vector<SlabImage> images;    // on-chip CSR images, one per cluster size used
+  struct Tuning {
+    int32_t C, prec, kernel;
+  };
+  std::vector<Tuning> tuning;       // autotuned launch shapes (deco_autotune / deco_set_tuning)
   // device arrays
   int32_t* row_ptr = nullptr;   // n+1
   int32_t* col_idx = nullptr;   // nnz, plain indices

@@ -60,7 +60,32 @@ static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int wa
   return per_cta * waves;
 }
 
+static std::mutex g_image_mutex;
+
+int tuned_selector(const deco_graph* g, int32_t C, int prec) {
+  std::lock_guard<std::mutex> lock(g_image_mutex);
+  for (const auto& t : g->tuning)
+    if (t.C == C && t.prec == prec) return t.kernel;
+  return -1;
+}
+
+void record_tuning(const deco_graph* g, int32_t C, int prec, int kernel) {
+  std::lock_guard<std::mutex> lock(g_image_mutex);
+  auto& tv = const_cast<deco_graph*>(g)->tuning;
+  for (auto& t : tv)
+    if (t.C == C && t.prec == prec) { t.kernel = kernel; return; }
+  tv.push_back({C, prec, kernel});
+}
+
 int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, PhasePlan* plan) {
+  if (force == DECO_KERNEL_AUTO) {
+    const int tuned = tuned_selector(g, C, prec);
+    if (tuned > 0) {
+      const int rc = plan_phase(g, C, ld, prec, tuned, plan);
+      if (rc == DECO_OK) return rc;
+      clear_error();   // a recorded shape that no longer fits: fall back to the cost model
+    }
+  }
   *plan = PhasePlan{};
   plan->kernel = KERNEL_GLOBAL;
   const int cols = prec == DECO_PREC_BF16 ? 64 : 32;
@@ -108,8 +133,6 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   }
   return DECO_OK;
 }
-
-static std::mutex g_image_mutex;
 
 int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec_, int force,
                          cudaStream_t st) {

@@ -20,6 +20,9 @@ struct PhasePlan {
 };
 
 int device_sm_count();
+// recorded launch shape for (C, prec) on g, or -1
+int tuned_selector(const deco_graph* g, int32_t C, int prec);
+void record_tuning(const deco_graph* g, int32_t C, int prec, int kernel);
 // force: DECO_KERNEL_* optionally | DECO_KERNEL_CLUSTER(k)
 int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, PhasePlan* plan);
 

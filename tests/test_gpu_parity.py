@@ -441,3 +441,27 @@ def test_solve_kernels_agree():
                                      deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM, kernel=kern), 5)
         out.append((res.best_cut, res.best_init, res.best_phase, z.tobytes(), pc.tobytes()))
     assert out[0] == out[1]
+
+
+# ------------------------------------------------------------------ autotuner
+
+@pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
+def test_autotune_records_a_shape_that_keeps_results(precision):
+    g = gg.torus_graph(40, 20, 2)
+    G = deco.graph_from(g)
+    C, ld = 256, 256
+    sel, us = deco.deco_autotune(G, C, precision, deco.DECO_OBJ_LAPLACIAN, 0.9, 10)
+    assert us > 0.0
+    kind = sel & 0xFF
+    assert kind in (deco.DECO_KERNEL_GLOBAL, deco.DECO_KERNEL_ONCHIP)
+    y, v = _phase_blocks(g, C, ld, precision, 9, 0.9)
+    ref = _run_phase(g, y, v, C, ld, 6, O.OBJ_LAPLACIAN, precision, 0.003, 0.9, deco.DECO_KERNEL_GLOBAL)
+    # the tuned shape is used by DECO_KERNEL_AUTO on the same handle
+    y2, v2 = y.clone(), v.clone()
+    a = deco.step_args(deco.DECO_OBJ_LAPLACIAN, precision, 0.003, 0.9)
+    deco.deco_run_phase(G, C, ld, y2, v2, 6, a, deco.DECO_KERNEL_AUTO)
+    torch.cuda.synchronize()
+    assert torch.equal(y2[:, :C], ref[0][:, :C]) and torch.equal(v2[:, :C], ref[1][:, :C])
+    with pytest.raises(deco.DecoError):
+        deco.deco_set_tuning(G, C, precision, 0x7777)
+    deco.deco_set_tuning(G, C, precision, deco.DECO_KERNEL_GLOBAL)
