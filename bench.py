@@ -43,6 +43,15 @@ def graphs():
     return [gg.er_graph(800, 0.06, 1), gg.torus_graph(40, 20, 2)]
 
 
+ER1M_B = 128
+ER1M_STEPS = 1000
+
+
+def er1m_graph():
+    """Large sparse workload: ER with n = 10^6 and average degree 10."""
+    return gg.er_graph_avg_degree(1_000_000, 10, 4)
+
+
 def edge_updates(gs, sched=SCHEDULE, b=B):
     return sum(g.nnz * b * l * s for g in gs for (l, s, _, _) in sched)
 
@@ -282,34 +291,40 @@ def run_reference(args, rank, world):
             "sample": f"per step: first phase only, {cols} of {B} starting points, {steps} of 2000 steps, both graphs"}
 
 
-def profile_kernel(sel: int, precision: str):
-    """Two launches of the dominant kernel (one 800-step unlifted phase of the
-    ER graph, C = 1024) with a fixed launch-shape selector, for ncu captures
-    (capture the second launch)."""
+def profile_kernel(sel: int, precision: str, workload: str = "er800"):
+    """Two phases of the dominant kernel with a fixed launch-shape selector,
+    for ncu captures (capture the second launch).
+      er800: one 800-step unlifted phase of ER(800, 0.06), C = 1024, mu = 0.9
+      er1m:  two steps of ER(10^6, avg degree 10), C = 128, mu = 0"""
     import torch
     import paper_2509_18612_gb300 as deco
-    g = graphs()[0]
+    if workload == "er1m":
+        g, C, steps, mu = er1m_graph(), ER1M_B, 2, 0.0
+    else:
+        g, C, steps, mu = graphs()[0], B, ROOF_STEPS, 0.9
     G = deco.graph_from(g)
     prec = deco.DECO_PREC_BF16 if precision == "bf16" else deco.DECO_PREC_FP32
     dt = torch.bfloat16 if precision == "bf16" else torch.float32
-    y0 = (torch.rand(g.n, B, device="cuda") * 2e-4 - 1e-4).to(dt)
-    v = torch.zeros(g.n, B, device="cuda")
-    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, prec, 0.01, 0.9)
+    y0 = (torch.rand(g.n, C, device="cuda") * 2e-4 - 1e-4).to(dt)
+    v = torch.zeros(g.n, C, device="cuda") if mu else None
+    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, prec, 0.01, mu)
     for i in range(2):
         y = y0.clone()
-        v.zero_()
+        if v is not None:
+            v.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        deco.deco_run_phase(G, B, B, y, v, ROOF_STEPS, a, sel)
+        deco.deco_run_phase(G, C, C, y, v, steps, a, sel)
         e1.record()
         torch.cuda.synchronize()
-        print(json.dumps({"launch": i, "selector": hex(sel), "us_per_step": e0.elapsed_time(e1) * 1e3 / ROOF_STEPS}))
+        print(json.dumps({"launch": i, "selector": hex(sel), "us_per_step": e0.elapsed_time(e1) * 1e3 / steps}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", type=lambda s: int(s, 0), default=None,
                     help="run only the dominant kernel twice with this launch-shape selector")
+    ap.add_argument("--profile-workload", default="er800", choices=["er800", "er1m"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -321,7 +336,7 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.profile_kernel is not None:
-        profile_kernel(args.profile_kernel, args.precision)
+        profile_kernel(args.profile_kernel, args.precision, args.profile_workload)
         return
     if args.impl == "reference":
         if rank != 0:

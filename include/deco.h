@@ -105,6 +105,12 @@ typedef enum deco_status {
  * memory stores, or through L2 (global stores + one bulk copy per CTA). */
 #define DECO_KERNEL_EXCHANGE_DSMEM (1 << 14)
 #define DECO_KERNEL_EXCHANGE_L2 (2 << 14)
+/* With DECO_KERNEL_GLOBAL, runs the block as 2^s column slabs (s = 1..6), one
+ * after another: the block is copied into dense n x w slabs (w = C / 2^s
+ * rounded up to 8) and every step of a slab runs before the next slab, so a
+ * narrow slab of a graph too large for shared memory stays in L2.  Needs
+ * ld >= round_up(C, 8 * 2^s). */
+#define DECO_KERNEL_COLUMN_SLABS(s) ((s) << 16)
 
 /* deco_create_graph flags */
 #define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */

@@ -62,9 +62,10 @@ extern "C" int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* 
   if (!y) { set_error("NULL block"); return DECO_ERR_ARG; }
   if (steps < 0) { set_error("steps must be >= 0"); return DECO_ERR_ARG; }
   const int kind = kernel & 0xFF, want_k = (kernel >> 8) & 0xF, want_t = (kernel >> 12) & 0x3;
-  const int want_x = (kernel >> 14) & 0x3;
-  if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_ONCHIP || (kernel & ~0xFFFF) || want_t == 3 ||
+  const int want_x = (kernel >> 14) & 0x3, want_s = (kernel >> 16) & 0xF;
+  if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_ONCHIP || (kernel & ~0xFFFFF) || want_t == 3 ||
       want_x == 3 || ((want_k || want_t || want_x) && kind != DECO_KERNEL_ONCHIP) ||
+      (want_s && (kind != DECO_KERNEL_GLOBAL || want_s > 6)) ||
       (want_k && ((want_k & (want_k - 1)) || want_k > 8))) {
     set_error("bad kernel selector 0x%x", kernel);
     return DECO_ERR_ARG;
@@ -83,9 +84,10 @@ extern "C" int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* 
   rc = R.run(yb, cur, v, steps, a->objective, a->alpha, a->momentum, a->alpha_cols, a->steps_cols,
              mom, mom, nonfinite_flag, st, nullptr);
   if (rc == DECO_OK && cur != 0) {
-    cudaError_t e = cudaMemcpyAsync(y, yb[1], (size_t)g->n * ld * elem_size(a->precision),
-                                    cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(run_phase)");
+    const size_t esz = elem_size(a->precision);
+    cudaError_t e = cudaMemcpy2DAsync(y, (size_t)ld * esz, yb[1], (size_t)ld * esz, (size_t)C * esz, g->n,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpy2DAsync(run_phase)");
   }
   R.release(st);
   return rc;

@@ -22,9 +22,11 @@ __global__ void k_probe_fill(int64_t count, int prec, uint32_t seed, void* y) {
 
 bool valid_selector(int kernel) {
   const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
-  if (kernel & ~0xFFFF) return false;
+  const int s = (kernel >> 16) & 0xF;
+  if (kernel & ~0xFFFFF) return false;
   if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_ONCHIP || t == 3 || x == 3) return false;
   if ((k || t || x) && kind != DECO_KERNEL_ONCHIP) return false;
+  if (s && (kind != DECO_KERNEL_GLOBAL || s > 6)) return false;
   if (k && ((k & (k - 1)) || k > 8)) return false;
   return true;
 }
@@ -57,6 +59,7 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
   const size_t esz = elem_size(precision);
 
   std::vector<int> cands = {DECO_KERNEL_GLOBAL};
+  for (int s = 1; s <= 4; ++s) cands.push_back(DECO_KERNEL_GLOBAL | (s << 16));   // 2..16 column slabs
   for (int k = 1; k <= 8; k *= 2)
     for (int t = 1; t <= 2; ++t)
       for (int x = 1; x <= 2; ++x) {

@@ -135,6 +135,9 @@ struct StepLaunch {
   int32_t* flag;
 };
 int launch_step_global(const StepLaunch& s, cudaStream_t st);
+// row-major n x ld (columns < C)  <->  S dense slabs of n x w (column c in slab c / w)
+int launch_slab_layout(int32_t n, int32_t ld, int32_t C, int32_t w, int32_t S, size_t esz, const void* src,
+                       void* dst, bool to_slabs, cudaStream_t st);
 
 int launch_pack(const deco_graph* g, int32_t B, int32_t lift, int32_t ld, int precision,
                 const void* y, uint32_t* zbits, cudaStream_t st);

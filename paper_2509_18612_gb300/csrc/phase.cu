@@ -92,10 +92,24 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_k = (force >> 8) & 0xF;
   const int want_t = (force >> 12) & 0x3;
   const int want_x = (force >> 14) & 0x3;
+  const int want_s = (force >> 16) & 0xF;
   force &= 0xFF;
   plan->threads = want_t == 1 ? 512 : 1024;
   plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
-  if (force == DECO_KERNEL_GLOBAL) return DECO_OK;
+  if (force == DECO_KERNEL_GLOBAL) {
+    if (want_s) {
+      // column slabs of width w, run one after another in a slab-major copy
+      const int S = 1 << want_s;
+      const int w = ((C + 8 * S - 1) / (8 * S)) * 8;
+      if (w * S > ld) {
+        set_error("%d column slabs do not fit ld = %d for C = %d", S, ld, C);
+        return DECO_ERR_UNSUPPORTED;
+      }
+      plan->col_slabs = S;
+      plan->slab_w = w;
+    }
+    return DECO_OK;
+  }
   const bool aligned = ld % cols == 0;
   const int max_smem = slab_max_smem();
   const int items = (C + cols - 1) / cols;
@@ -207,6 +221,56 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
   sl.dnet = g->dnet;
   sl.v = v; sl.alpha = alpha; sl.mu = mu;
   sl.alpha_cols = alpha_cols; sl.steps_cols = steps_cols; sl.flag = flag;
+  if (plan.col_slabs > 1 && steps > 0) {
+    // Column-slab schedule: copy the block into S dense n x w slabs, run all
+    // steps of one slab before the next (a narrow dense slab and the CSR stay
+    // resident in L2), copy back.  Columns are independent (remark after
+    // Eq. 11), so the arithmetic of every column is unchanged.
+    const int S = plan.col_slabs, w = plan.slab_w;
+    const size_t esz = prec == DECO_PREC_BF16 ? 2 : 4;
+    const bool momv = mu != 0.0f && v != nullptr;
+    if (!ypart) {
+      cudaError_t e = cudaMallocAsync((void**)&ypart, (size_t)g->n * w * S * esz, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(slab partner)");
+    }
+    // y[cur] is only read (into slab-major A) and, at the end, its columns
+    // < C are rewritten; its padding columns are never touched
+    unsigned char* A = static_cast<unsigned char*>(y[cur ^ 1]);   // slab-major data
+    unsigned char* Bp = ypart;                                    // ping-pong partner
+    int rc = launch_slab_layout(g->n, ld, C, w, S, esz, y[cur], A, true, st);
+    if (rc) return rc;
+    if (momv) {
+      if (!vslab) {
+        cudaError_t e = cudaMallocAsync((void**)&vslab, (size_t)g->n * w * S * sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(slab momentum)");
+      }
+      if ((rc = launch_slab_layout(g->n, ld, C, w, S, 4, v, vslab, true, st))) return rc;
+    }
+    for (int s = 0; s < S; ++s) {
+      const int c0 = s * w;
+      const int Cs = std::min(w, C - c0);
+      if (Cs <= 0) break;
+      sl.C = Cs;
+      sl.ld = w;
+      sl.alpha_cols = alpha_cols ? alpha_cols + c0 : nullptr;
+      sl.steps_cols = steps_cols ? steps_cols + c0 : nullptr;
+      sl.v = momv ? vslab + (size_t)c0 * g->n : nullptr;
+      unsigned char* blk[2] = {A + (size_t)c0 * g->n * esz, Bp + (size_t)c0 * g->n * esz};
+      int c = 0;
+      for (int32_t t = 0; t < steps; ++t) {
+        sl.yin = blk[c];
+        sl.yout = blk[c ^ 1];
+        sl.t = t;
+        if ((rc = launch_step_global(sl, st))) return rc;
+        c ^= 1;
+      }
+    }
+    unsigned char* res = (steps % 2 == 0) ? A : Bp;
+    if ((rc = launch_slab_layout(g->n, ld, C, w, S, esz, res, y[cur], false, st))) return rc;
+    if (momv && (rc = launch_slab_layout(g->n, ld, C, w, S, 4, vslab, v, false, st))) return rc;
+    if (kernels) *kernels += (int64_t)steps * S + 2 + (momv ? 2 : 0);
+    return DECO_OK;
+  }
   for (int32_t t = 0; t < steps; ++t) {
     sl.yin = y[cur];
     sl.yout = y[cur ^ 1];
@@ -221,7 +285,11 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
 
 void PhaseRunner::release(cudaStream_t st) {
   if (xbuf) cudaFreeAsync(xbuf, st);
+  if (vslab) cudaFreeAsync(vslab, st);
+  if (ypart) cudaFreeAsync(ypart, st);
   xbuf = nullptr;
+  vslab = nullptr;
+  ypart = nullptr;
 }
 
 }  // namespace deco

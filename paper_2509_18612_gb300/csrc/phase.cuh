@@ -14,6 +14,8 @@ struct PhasePlan {
   int k = 1;                     // cluster size of the on-chip kernel
   int threads = 1024;            // CTA size of the on-chip kernel
   int xmode = 2;                 // exchange between cluster CTAs: 1 DSMEM, 2 L2
+  int col_slabs = 1;             // global kernel: column slabs run one after another (slab-major)
+  int slab_w = 0;                // their width
   int items = 0;                 // column slabs
   int32_t max_own = 0, max_img_words = 0;
   SlabImage image;               // on-chip CSR image (owned by the graph)
@@ -32,6 +34,8 @@ struct PhaseRunner {
   int prec = 0;
   PhasePlan plan;
   unsigned char* xbuf = nullptr;  // exchange buffer of the on-chip kernel (k > 1)
+  float* vslab = nullptr;         // slab-major momentum of the column-slab schedule
+  unsigned char* ypart = nullptr; // slab-major ping-pong partner of the column-slab schedule
 
   // choose the kernel for a C-column block of g (builds the CSR image once)
   int prepare(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, cudaStream_t st);

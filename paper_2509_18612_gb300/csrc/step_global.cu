@@ -11,6 +11,8 @@
 // neighbour loop is unrolled four ways so four independent gathers are in
 // flight per lane.  Used for graphs whose iterate does not fit on chip and as
 // the reference launch shape for the persistent kernels.
+#include <algorithm>
+
 #include "deco_internal.cuh"
 
 namespace deco {
@@ -98,6 +100,36 @@ __global__ void __launch_bounds__(256) k_step_global(KArgs a) {
   for (int k = 0; k < VN; ++k) acc[k] = 0.0f;
   const int32_t e0 = __ldg(a.row_ptr + r), e1 = __ldg(a.row_ptr + r + 1);
   int32_t e = e0;
+  // eight independent gathers in flight per lane (raw 16-byte vectors, unpacked
+  // when accumulated); neighbours are still added in CSR order
+  for (; e + 8 <= e1; e += 8) {
+    int32_t j[8];
+    float wt[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) edge_at<WMODE>(a, e + q, j[q], wt[q]);
+    uint4 raw[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t off = (size_t)j[q] * a.ld + c0;
+      raw[q] = PREC == DECO_PREC_FP32
+                   ? __ldg(reinterpret_cast<const uint4*>(static_cast<const float*>(a.yin) + off))
+                   : __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(a.yin) + off));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float val[VN];
+      if (PREC == DECO_PREC_FP32) {
+        val[0] = __uint_as_float(raw[q].x); val[1] = __uint_as_float(raw[q].y);
+        val[2] = __uint_as_float(raw[q].z); val[3] = __uint_as_float(raw[q].w);
+      } else {
+        const uint32_t u[4] = {raw[q].x, raw[q].y, raw[q].z, raw[q].w};
+#pragma unroll
+        for (int h = 0; h < VN / 2; ++h) { val[2 * h] = bf16lo(u[h]); val[2 * h + 1] = bf16hi(u[h]); }
+      }
+#pragma unroll
+      for (int k = 0; k < VN; ++k) acc[k] = (WMODE == W_UNIT) ? acc[k] + val[k] : fmaf(wt[q], val[k], acc[k]);
+    }
+  }
   for (; e + 4 <= e1; e += 4) {
     int32_t j[4];
     float wt[4];
@@ -228,6 +260,41 @@ int launch_step_global(const StepLaunch& s, cudaStream_t st) {
   const bool lap = s.objective == DECO_OBJ_LAPLACIAN;
   if (s.precision == DECO_PREC_BF16) launch_p<DECO_PREC_BF16>(a, s.wmode, mom, lap, threads, st);
   else launch_p<DECO_PREC_FP32>(a, s.wmode, mom, lap, threads, st);
+  DECO_CUDA_TRY(cudaGetLastError());
+  return DECO_OK;
+}
+
+// ---- slab-major layout: row-major n x ld  <->  S slabs of dense n x w
+// element (r, c) of the row-major block is element (r, c % w) of slab c / w.
+namespace {
+template <typename T>
+__global__ void k_to_slabs(int32_t n, int32_t ld, int32_t C, int32_t w, int32_t S, const T* __restrict__ src,
+                           T* __restrict__ dst, int to_slabs) {
+  const int64_t total = (int64_t)n * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / C;
+    const int32_t c = (int32_t)(i % C);   // column of the row-major block
+    const int64_t slab_idx = (int64_t)(c / w) * n * w + r * w + (c % w);
+    if (to_slabs) dst[slab_idx] = src[r * ld + c];
+    else dst[r * ld + c] = src[slab_idx];
+  }
+}
+}  // namespace
+
+int launch_slab_layout(int32_t n, int32_t ld, int32_t C, int32_t w, int32_t S, size_t esz, const void* src,
+                       void* dst, bool to_slabs, cudaStream_t st) {
+  const int64_t total = (int64_t)n * C;
+  if (total == 0) return DECO_OK;
+  (void)S;
+  const int block = 256;
+  const unsigned grid = (unsigned)std::min<int64_t>((total + block - 1) / block, 152 * 32);
+  if (esz == 2)
+    k_to_slabs<uint16_t><<<grid, block, 0, st>>>(n, ld, C, w, S, static_cast<const uint16_t*>(src),
+                                                  static_cast<uint16_t*>(dst), to_slabs ? 1 : 0);
+  else
+    k_to_slabs<uint32_t><<<grid, block, 0, st>>>(n, ld, C, w, S, static_cast<const uint32_t*>(src),
+                                                  static_cast<uint32_t*>(dst), to_slabs ? 1 : 0);
   DECO_CUDA_TRY(cudaGetLastError());
   return DECO_OK;
 }

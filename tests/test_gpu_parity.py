@@ -443,6 +443,26 @@ def test_solve_kernels_agree():
     assert out[0] == out[1]
 
 
+@pytest.mark.parametrize("name", ["er800", "signed", "ba"])
+@pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_column_slab_schedule_bitwise_equals_global(name, precision, s):
+    g = GRAPHS[name]()
+    C, ld = 200, 256                                  # ragged last slab
+    objective = O.OBJ_LAPLACIAN if name == "signed" else O.OBJ_MULTILINEAR01
+    y, v = _phase_blocks(g, C, ld, precision, 4, 0.9)
+    steps_cols = to_dev(np.random.default_rng(5).integers(0, 9, C).astype(np.int32))
+    alpha_cols = to_dev(np.random.default_rng(6).uniform(1e-3, 2e-2, C).astype(np.float32))
+    for steps in (7, 8):                              # odd / even: result in either buffer
+        ref = _run_phase(g, y, v, C, ld, steps, objective, precision, 0.0, 0.9, deco.DECO_KERNEL_GLOBAL,
+                         alpha_cols, steps_cols)
+        got = _run_phase(g, y, v, C, ld, steps, objective, precision, 0.0, 0.9,
+                         deco.DECO_KERNEL_GLOBAL | (s << 16), alpha_cols, steps_cols)
+        assert torch.equal(got[0][:, :C], ref[0][:, :C])
+        assert torch.equal(got[1][:, :C], ref[1][:, :C])
+        assert torch.equal(got[0][:, C:], y[:, C:])   # padding columns untouched
+
+
 # ------------------------------------------------------------------ autotuner
 
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
