@@ -45,6 +45,11 @@ def graphs():
 
 ER1M_B = 128
 ER1M_STEPS = 1000
+# DRAM bytes (read + write) of one launch, from the ncu capture summarised in
+# profiles/: k_step_global on ER(1e6), 128 BF16 columns, plain schedule; and
+# k_slab on ER(800), 1024 FP32 columns, 800 steps, cluster 4 / 1024 threads / L2.
+K_STEP_ER1M_TRAFFIC = 2013752064 + 248812288
+K_SLAB_ER800_TRAFFIC = 6756352
 
 
 def er1m_graph():
@@ -191,7 +196,8 @@ def run_deco(args, rank, world):
         e2e = {"value": edge_updates(gs) / (t1 - t0), "unit": "edge-updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    roof = roofline_step(args, deco, torch, dev, handles[0], gs[0]) if rank == 0 else None
+    roof = (roofline_step(args, deco, torch, dev, handles[0], gs[0],
+                          tuned[f"er/C{B}/{args.precision}"]) if rank == 0 else None)
 
     # ---- the other precision of the same workload (FP32 vs BF16-X/FP32-accum)
     other = None
@@ -223,7 +229,7 @@ def run_deco(args, rank, world):
 ROOF_STEPS = 800
 
 
-def roofline_step(args, deco, torch, dev, G, g):
+def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
     """Dominant kernel: the persistent on-chip phase kernel (k_slab) running one
     800-step unlifted phase of the ER graph over all C = 1024 columns, timed
     with CUDA events on its launch stream (average over a few launches).
@@ -261,8 +267,10 @@ def roofline_step(args, deco, torch, dev, G, g):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_onchip = 152 * 128 * sm_mhz * 1e6 / 1e9      # GB/s through the SM load path
     ach = gathered / t / 1e9
+    sel = tuned_selector_hint
     return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
-            "traffic": None, "kernel": "k_slab (persistent on-chip PGA phase, fused gather + step)",
+            "traffic": K_SLAB_ER800_TRAFFIC if sel == "0xa402" and args.precision == "fp32" else None,
+            "kernel": "k_slab (persistent on-chip PGA phase, fused gather + step)", "selector": sel,
             "launch_us": t * 1e6, "steps_per_launch": ROOF_STEPS, "us_per_step": t * 1e6 / ROOF_STEPS,
             "algorithmic_bytes_per_launch": gathered, "compulsory_dram_bytes_per_launch": compulsory,
             "peak_kind": "derived: 152 SMs x 128 B/clk (shared-memory load path) x sm_max_mhz ("
@@ -289,6 +297,90 @@ def run_reference(args, rank, world):
     value = sample_units / t_total
     return {"value": value, "ms": t_total * 1e3 / max(args.steps, 1),
             "sample": f"per step: first phase only, {cols} of {B} starting points, {steps} of 2000 steps, both graphs"}
+
+
+def run_er1m():
+    """Large sparse workload: ER(n = 10^6, average degree 10), B = 128 starts
+    with BF16 iterates, one unlifted phase of T = 1000 steps (alpha = 0.01,
+    plain PGA), IDI-centred starts; rounding, cuts and argmax included.
+
+    Roofline of its dominant kernel (the per-step kernel in the tuned shape),
+    HBM-bound: algorithmic bytes per step = CSR (4 nnz + 4 (n+1)) + read and
+    write of the BF16 block (2 n C 2 B)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    from paper_2509_18612_gb300.tuning import TuningTable
+    g = er1m_graph()
+    G = deco.graph_from(g)
+    C = ER1M_B
+    sel, us_probe = deco.deco_autotune(G, C, deco.DECO_PREC_BF16, deco.DECO_OBJ_MULTILINEAR01, 0.0, 20)
+    p = deco.params(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16)
+    sched = [(1, ER1M_STEPS, 0.01, 0.0)]
+    deco.deco_solve(G, C, [(1, 20, 0.01, 0.0)], p, 1, want_assignment=False, want_phase_cuts=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res, z, _ = deco.deco_solve(G, C, sched, p, 2, want_phase_cuts=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    # dominant kernel: CUDA events around 50 steps of the tuned launch shape
+    y = (torch.rand(g.n, C, device="cuda") * 2e-4 - 1e-4).to(torch.bfloat16)
+    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, deco.DECO_PREC_BF16, 0.01, 0.0)
+    deco.deco_run_phase(G, C, C, y, None, 4, a, sel)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record()
+    deco.deco_run_phase(G, C, C, y, None, 50, a, sel)
+    k1.record()
+    torch.cuda.synchronize()
+    t_step = k0.elapsed_time(k1) / 1e3 / 50
+    alg = 4 * g.nnz + 4 * (g.n + 1) + 2 * g.n * C * 2
+    peaks, kind = measured_peaks()
+    ach = alg / t_step / 1e9
+    return {"workload": "ER(n=1e6, avg deg 10); B=128 bf16 starts (IDI); pQUCO T=1000, alpha=0.01",
+            "value": res.edge_updates / t, "unit": "edge-updates/s", "solve_s": t, "best_cut": res.best_cut,
+            "m": g.m, "tuned_kernel": hex(sel), "gpu_launches": res.kernel_launches,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"],
+                         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
+                         # kernel in this shape (profiles/k_step_global_er1m_bf16.md)
+                         "traffic": K_STEP_ER1M_TRAFFIC if sel == 0x1 else None, "peak_kind": kind,
+                         "kernel": "k_step_global (one step)", "us_per_launch": t_step * 1e6,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
+def run_ba256():
+    """Batched workload: 256 Barabasi-Albert graphs (n ~ U{200..1200}, m = 4),
+    B = 256 starts each, population of 32 (alpha, T) candidates x 8 starts,
+    5 evolution rounds alternating lift 1 / 2, T ~ U{500..2000},
+    e ~ U[-4, -1], momentum 0.9, IDI + uniform starts, FP32; all graphs run in
+    the same launches, rounds after the first of a lift replay a CUDA graph."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    rng = np.random.default_rng(3000)
+    sizes = rng.integers(200, 1201, 256)
+    graphs_ = [gg.ba_graph(int(n), 4, 3000 + i) for i, n in enumerate(sizes)]
+    batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs_])
+    U = batch.graph()
+    for C in (256, 512):
+        deco.deco_autotune(U, C, deco.DECO_PREC_FP32, deco.DECO_OBJ_MULTILINEAR01, 0.9, 20)
+    pop = deco.population(candidates=32, rounds=5, t_lo=500, t_hi=2000, e_lo=-4.0, e_hi=-1.0, momentum=0.9,
+                          lifts=(1, 2))
+    p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM)
+    small = deco.population(candidates=32, rounds=2, t_lo=10, t_hi=10, lifts=(1, 2))
+    deco.deco_solve_batch(batch, 256, p, small, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, best, ex = deco.deco_solve_batch(batch, 256, p, pop, 2)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    return {"workload": "256 x BA(n~U{200..1200}, m=4); B=256; population 32 x 8; 5 rounds lift 1/2; "
+                        "T~U{500..2000}; e~U[-4,-1]; mu=0.9",
+            "value": res.edge_updates / (res.device_ms / 1e3), "unit": "edge-updates/s",
+            "device_s": res.device_ms / 1e3, "wall_s": t, "sum_best_cuts": int(best.sum()),
+            "sum_m": int(sum(g.m for g in graphs_)), "gpu_launches": res.kernel_launches,
+            "final_alpha": [float(10 ** x) for x in ex["final_e"][:4]], "final_T": ex["final_T"][:4].tolist(),
+            "round_best_score": [int(s.max()) for s in ex["round_scores"]]}
 
 
 def profile_kernel(sel: int, precision: str, workload: str = "er800"):
@@ -332,6 +424,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--polish", type=int, default=50)
     ap.add_argument("--no-other", action="store_true", help="skip the other-precision measurement")
+    ap.add_argument("--main-only", action="store_true",
+                    help="measure only the main workload (skip the 1M-node and 256-graph workloads)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -360,6 +454,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     r = run_deco(args, rank, world)
+    extra = {}
+    if rank == 0 and not args.main_only:
+        extra["er1m_sparse"] = run_er1m()
+        extra["ba256_population"] = run_ba256()
     if rank == 0:
         cpu = None
         if world == 1:
@@ -375,7 +473,7 @@ def main():
                 "clocks": r["clocks"], "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
                 "gpu_launches": r["gpu_launches"], "other_precision": r["other_precision"],
                 "tuned_kernels": r["tuned"],
-                "best_cuts": r["best_cuts"]}
+                "best_cuts": r["best_cuts"], "workloads": extra}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

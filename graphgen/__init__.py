@@ -161,25 +161,28 @@ def ba_graph(n: int, m: int, seed: int) -> Graph:
     if n <= m:
         raise ValueError("BA graph needs n > m")
     rng = np.random.default_rng(seed)
-    us, vs = [], []
-    targets_pool = []
+    n_edges = (m + 1) * m // 2 + (n - m - 1) * m
+    us = np.empty(n_edges, dtype=np.int64)
+    vs = np.empty(n_edges, dtype=np.int64)
+    pool = np.empty(2 * n_edges, dtype=np.int64)   # every edge end once: degree-proportional draws
+    k = 0
     for a in range(m + 1):
         for b in range(a):
-            us.append(a)
-            vs.append(b)
-            targets_pool += [a, b]
+            us[k], vs[k] = a, b
+            pool[2 * k], pool[2 * k + 1] = a, b
+            k += 1
     for node in range(m + 1, n):
-        chosen = set()
-        pool = np.asarray(targets_pool)
+        size = 2 * k
+        chosen = []
         while len(chosen) < m:
-            picks = pool[rng.integers(0, pool.size, size=2 * m)]
-            for t in picks:
-                if len(chosen) < m:
-                    chosen.add(int(t))
+            for t in pool[rng.integers(0, size, size=2 * m)]:
+                t = int(t)
+                if t not in chosen and len(chosen) < m:
+                    chosen.append(t)
         for t in sorted(chosen):
-            us.append(node)
-            vs.append(t)
-            targets_pool += [node, t]
+            us[k], vs[k] = node, t
+            pool[2 * k], pool[2 * k + 1] = node, t
+            k += 1
     return from_edges(n, us, vs, name=f"ba{n}_m{m}_s{seed}")
 
 

@@ -323,6 +323,58 @@ int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t
                const deco_params* p, uint64_t seed, const float* x0, const float* mean,
                uint8_t* assignment, int64_t* phase_cuts, void* stream, deco_result* out);
 
+/* ---------------------------------------------------------------- batches
+ * Many graphs solved together with the evolution-based hyper-parameter
+ * search of Sec. 4.3.  A batch is the disjoint union of its graphs (a
+ * block-diagonal adjacency), so every step kernel runs over all of them in
+ * the same launches; rounding, cuts, argmax and best records stay per graph. */
+typedef struct deco_batch deco_batch;
+
+/* Build a batch from existing graphs (copied; the graphs may be destroyed
+ * afterwards).  Errors: DECO_ERR_ARG, DECO_ERR_OOM, DECO_ERR_CUDA. */
+int deco_create_batch(const deco_graph* const* graphs, int32_t n_graphs, deco_batch** out);
+void deco_destroy_batch(deco_batch* b);
+/* The union graph of a batch (owned by the batch), e.g. for deco_autotune. */
+int deco_batch_graph(const deco_batch* b, const deco_graph** out);
+
+/* Population of Sec. 4.3, shared by every graph of the batch.
+ *  candidates  P; candidate k owns starts [k B/P, (k+1) B/P) of every graph.
+ *  rounds      evolution rounds; round r runs one phase with lift
+ *              lifts[r % n_lifts] (e.g. {1, 2}: the pDECO alternation).
+ *  t_lo, t_hi  step budgets: T ~ U{t_lo..t_hi}, T' clipped to [t_lo, t_hi].
+ *  e_lo, e_hi  alpha = 10^e, e ~ U[e_lo, e_hi], e' = Proj[e_lo, e_hi](e + 0.2 N(0,1)).
+ * Candidate k's score is the sum over graphs of the best cut among its
+ * starts; after every round the top half is kept (ties: lower index) and
+ * the j-th worst member is replaced by a perturbed copy of the j-th best. */
+typedef struct deco_population {
+  int32_t candidates;
+  int32_t rounds;
+  int32_t t_lo, t_hi;
+  float e_lo, e_hi;
+  float momentum;
+  int32_t n_lifts;
+  int32_t lifts[8];
+} deco_population;
+
+/* Batched pDECO with population search (Sec. 4.2, 4.3, Alg. 3).
+ *  B           starts per graph, a multiple of pop->candidates.
+ *  p           objective, precision (no FP32 polish), init (UNIFORM, IDI or
+ *              IDI_HALF_UNIFORM; graph i draws with key seed + i), kernel.
+ *  best_cuts   host, n_graphs int64: best cut of every graph over all rounds.
+ *  assignment  host, sum of n bytes (graphs in batch order) or NULL.
+ *  round_cuts  host, rounds x n_graphs x B int64 or NULL.
+ *  round_scores host, rounds x P int64 or NULL.
+ *  final_e, final_T  host, P entries each or NULL: the last population.
+ *  out         best_cut = sum over graphs; edge_updates counts the longest
+ *              budget of every round for all columns.
+ * Rounds after the first of a lift replay a captured CUDA graph.  One host
+ * synchronisation per round (the evolution runs on the host, in FP64).
+ * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED, DECO_ERR_OOM, DECO_ERR_CUDA,
+ * DECO_ERR_NONFINITE, DECO_ERR_TIMEOUT. */
+int deco_solve_batch(const deco_batch* b, int32_t B, const deco_params* p, const deco_population* pop,
+                     uint64_t seed, int64_t* best_cuts, uint8_t* assignment, int64_t* round_cuts,
+                     int64_t* round_scores, float* final_e, int32_t* final_T, void* stream, deco_result* out);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);
 

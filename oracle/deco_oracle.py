@@ -529,6 +529,105 @@ def evolve(exponents, steps, scores, eps, eps_prime, t_lo: int, t_hi: int,
     return ne, nT, keep
 
 
+def population_init(P: int, t_lo: int, t_hi: int, e_lo: float, e_hi: float, seed: int):
+    """Initial population of Sec. 4.3: T ~ U{T_l, T_u}, e ~ U[e_l, e_u], alpha = 10^e.
+
+    Draws: counter (k, 0, 0, STREAM_EVOLVE) for candidate k; e from word 0
+    (e_l + (e_u - e_l) u), T from word 1 (T_l + word mod (T_u - T_l + 1)).
+    """
+    k = np.arange(P, dtype=np.uint64)
+    x0, x1, _, _ = draw_words(k, 0, 0, STREAM_EVOLVE, seed)
+    e = e_lo + (e_hi - e_lo) * u01_from_bits(x0)
+    T = t_lo + (x1.astype(np.int64) % (t_hi - t_lo + 1))
+    return e.astype(np.float64), T.astype(np.int64)
+
+
+def population_perturbations(n_replaced: int, round_idx: int, seed: int):
+    """eps ~ N(0,1) and eps' ~ U(0,1) of the j-th replaced member in a round:
+    counter (j, round, 1, STREAM_EVOLVE); eps by Box-Muller of words 0 and 1,
+    eps' from word 2."""
+    j = np.arange(n_replaced, dtype=np.uint64)
+    x0, x1, x2, _ = draw_words(j, round_idx, 1, STREAM_EVOLVE, seed)
+    u1, u2 = u01_from_bits(x0), u01_from_bits(x1)
+    eps = np.array([math.sqrt(-2.0 * math.log(a)) * math.cos(2.0 * math.pi * b) for a, b in zip(u1, u2)])
+    return eps, u01_from_bits(x2)
+
+
+def alpha_of(e) -> np.ndarray:
+    """alpha = 10^e, evaluated with the C library's pow and rounded to FP32 (the
+    step size the iteration uses)."""
+    return np.array([np.float32(math.pow(10.0, float(x))) for x in np.atleast_1d(e)], dtype=np.float64)
+
+
+@dataclass
+class BatchResult:
+    best_cuts: List[int]
+    round_cuts: List[np.ndarray]      # per round: n_graphs x B
+    round_scores: List[np.ndarray]    # per round: P
+    populations: List[tuple]          # per round: (e, T) used in that round
+    final_e: np.ndarray = None
+    final_T: np.ndarray = None
+
+
+def solve_batch_population(graphs, B: int, P: int, rounds: int, lifts, t_lo: int, t_hi: int,
+                           e_lo: float, e_hi: float, momentum: float, params: Params, seed: int) -> BatchResult:
+    """Batched pDECO with the evolution-based search of Sec. 4.3, one shared
+    population for all graphs of the batch.
+
+    Candidate k owns starts [k B/P, (k+1) B/P); in a round it runs T_k steps
+    with alpha_k = 10^{e_k} (per-column step size and step budget).  Round r
+    uses lift lifts[r mod len(lifts)] (Alg. 3 alternation).  Its starts are
+    drawn per graph (round 0: params.init; later rounds: Gaussian around
+    2 z* - 1 of that graph's best binary vector of the previous round,
+    Sec. 4.2).  After the round every start is rounded and cut per graph; the
+    score of candidate k is the sum over graphs of the best cut among its
+    starts; the population then evolves (``evolve``) with T' clipped to
+    [t_lo, t_hi].  Readings: the population is shared by the batch (one
+    hyper-parameter set for a dataset); random draws as in
+    ``population_init`` / ``population_perturbations``; graph i draws its
+    starts with key seed + i, counters indexed by its own rows, and the
+    phase index of those counters is the round index.
+    """
+    e, T = population_init(P, t_lo, t_hi, e_lo, e_hi, seed)
+    per = B // P
+    best = [None] * len(graphs)
+    prev_z = [None] * len(graphs)
+    res = BatchResult(best_cuts=[], round_cuts=[], round_scores=[], populations=[])
+    for r in range(rounds):
+        lift = lifts[r % len(lifts)]
+        C = B * lift
+        cand_of_col = (np.arange(C) // lift) // per
+        alpha_cols = alpha_of(e)[cand_of_col]
+        steps_cols = T[cand_of_col]
+        res.populations.append((e.copy(), T.copy()))
+        cuts_r = np.zeros((len(graphs), B), dtype=np.int64)
+        for gi, g in enumerate(graphs):
+            gseed = (seed + gi) & 0xFFFFFFFFFFFFFFFF
+            if r == 0:
+                Y = initial_block(g, B, lift, params, gseed)
+            else:
+                Y = gaussian_block(2.0 * prev_z[gi].astype(np.float64) - 1.0, C, gseed, r, params.eta, params.scale)
+            Y = run_phase(g, Y, Phase(lift, int(steps_cols.max()), 0.0, momentum), params.objective,
+                          alpha_cols=alpha_cols, active_steps=steps_cols)
+            Z = binarize(Y, lift)
+            cuts = cut_values(g, Z)
+            cuts_r[gi] = cuts
+            b = best_of(cuts)
+            prev_z[gi] = Z[:, b].copy()
+            if best[gi] is None or int(cuts[b]) > best[gi]:
+                best[gi] = int(cuts[b])
+        scores = np.array([int(cuts_r[:, k * per:(k + 1) * per].max(axis=1).sum()) for k in range(P)])
+        res.round_cuts.append(cuts_r)
+        res.round_scores.append(scores)
+        if r + 1 < rounds:
+            n_rep = P - P // 2
+            eps, epsp = population_perturbations(n_rep, r, seed)
+            e, T, _ = evolve(e, T, scores, eps, epsp, t_lo, t_hi, e_lo, e_hi)
+    res.best_cuts = best
+    res.final_e, res.final_T = e, T
+    return res
+
+
 # ----------------------------------------------------------------------------
 # Exhaustive and greedy references
 # ----------------------------------------------------------------------------

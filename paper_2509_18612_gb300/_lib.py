@@ -48,7 +48,8 @@ DECO_KERNEL_ONCHIP = 2
 EXPORTED = [
     "deco_create_graph", "deco_destroy_graph", "deco_graph_info", "deco_eval_cut",
     "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_run_phase_noalloc", "deco_round_cut",
-    "deco_init_block", "deco_autotune", "deco_set_tuning",
+    "deco_init_block", "deco_autotune", "deco_set_tuning", "deco_create_batch", "deco_destroy_batch",
+    "deco_batch_graph", "deco_solve_batch",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
 ]
 
@@ -79,6 +80,12 @@ class deco_phase(ctypes.Structure):
                 ("alpha", ctypes.c_float), ("momentum", ctypes.c_float)]
 
 
+class deco_population(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("rounds", ctypes.c_int32), ("t_lo", ctypes.c_int32),
+                ("t_hi", ctypes.c_int32), ("e_lo", ctypes.c_float), ("e_hi", ctypes.c_float),
+                ("momentum", ctypes.c_float), ("n_lifts", ctypes.c_int32), ("lifts", ctypes.c_int32 * 8)]
+
+
 class deco_result(ctypes.Structure):
     _fields_ = [("best_cut", ctypes.c_int64), ("best_init", ctypes.c_int32),
                 ("best_phase", ctypes.c_int32), ("edge_updates", ctypes.c_int64),
@@ -102,6 +109,11 @@ def _load():
         "deco_run_phase_noalloc": (ctypes.c_int, [P, I32, I32, P, P, I32, ctypes.POINTER(deco_step_args), P, P]),
         "deco_autotune": (ctypes.c_int, [P, I32, I32, I32, F32, I32, P, P, P]),
         "deco_set_tuning": (ctypes.c_int, [P, I32, I32, I32]),
+        "deco_create_batch": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
+        "deco_destroy_batch": (None, [P]),
+        "deco_batch_graph": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+        "deco_solve_batch": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_params), ctypes.POINTER(deco_population),
+                                            U64, P, P, P, P, P, P, P, ctypes.POINTER(deco_result)]),
         "deco_round_cut": (ctypes.c_int, [P, I32, I32, I32, I32, P, P, P, P, P]),
         "deco_init_block": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(deco_params), U64, I32, P, P, P, P]),
         "deco_idi_mean": (ctypes.c_int, [P, F32, U64, I32, P, P]),
@@ -310,6 +322,73 @@ def deco_solve(g: Graph, B: int, phases: Sequence, p: deco_params, seed: int, x0
     _check(lib.deco_solve(g, int(B), arr, len(phases), ctypes.byref(p), int(seed), _ptr(x0p), _ptr(meanp),
                           _ptr(assignment), _ptr(pc), _stream(stream), ctypes.byref(res)))
     return res, assignment, pc
+
+
+class Batch:
+    """Owning handle of a deco_batch (the disjoint union of several graphs)."""
+
+    def __init__(self, handle: int, sizes):
+        self.handle = handle
+        self.sizes = list(sizes)
+        self.n = int(sum(self.sizes))
+
+    def close(self):
+        if self.handle:
+            lib.deco_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+    def graph(self) -> Graph:
+        """Non-owning view of the union graph (for deco_autotune / deco_set_tuning)."""
+        h = ctypes.c_void_p()
+        _check(lib.deco_batch_graph(self, ctypes.byref(h)))
+        view = Graph(h.value, self.n, 0)
+        view.close = lambda: None          # owned by the batch
+        return view
+
+
+def deco_create_batch(graphs: Sequence[Graph]) -> Batch:
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+    h = ctypes.c_void_p()
+    _check(lib.deco_create_batch(arr, len(graphs), ctypes.byref(h)))
+    return Batch(h.value, [g.n for g in graphs])
+
+
+def deco_destroy_batch(b: Batch):
+    b.close()
+
+
+def population(candidates=32, rounds=5, t_lo=500, t_hi=2000, e_lo=-4.0, e_hi=-1.0, momentum=0.9,
+               lifts=(1, 2)) -> deco_population:
+    arr = (ctypes.c_int32 * 8)(*(list(lifts) + [0] * (8 - len(lifts))))
+    return deco_population(candidates, rounds, t_lo, t_hi, e_lo, e_hi, momentum, len(lifts), arr)
+
+
+def deco_solve_batch(b: Batch, B: int, p: deco_params, pop: deco_population, seed: int,
+                     want_assignment=False, want_round_cuts=False, stream=None):
+    """Returns (deco_result, best_cuts[n_graphs], extras dict)."""
+    G = len(b.sizes)
+    best = np.zeros(G, dtype=np.int64)
+    assignment = np.zeros(b.n, dtype=np.uint8) if want_assignment else None
+    rc = np.zeros((pop.rounds, G, B), dtype=np.int64) if want_round_cuts else None
+    scores = np.zeros((pop.rounds, pop.candidates), dtype=np.int64)
+    fe = np.zeros(pop.candidates, dtype=np.float32)
+    fT = np.zeros(pop.candidates, dtype=np.int32)
+    res = deco_result()
+    _check(lib.deco_solve_batch(b, int(B), ctypes.byref(p), ctypes.byref(pop), int(seed), _ptr(best),
+                                _ptr(assignment), _ptr(rc), _ptr(scores), _ptr(fe), _ptr(fT), _stream(stream),
+                                ctypes.byref(res)))
+    return res, best, {"assignment": assignment, "round_cuts": rc, "round_scores": scores,
+                       "final_e": fe, "final_T": fT}
 
 
 def deco_abi_version() -> int:

@@ -1,0 +1,519 @@
+// Batched pDECO over many graphs with the evolution-based hyper-parameter
+// search of Sec. 4.3, one shared population for the batch.
+//
+// The batch is the disjoint union of its graphs (block-diagonal A), so every
+// step kernel runs over all graphs at once without knowing about them; a
+// row -> graph map drives the per-graph IDI thresholds, cut sums, argmax and
+// best records.  Candidate k of the population owns starts
+// [k B/P, (k+1) B/P) and runs T_k steps with alpha_k = 10^{e_k} through the
+// per-column step-size and step-budget arrays of the phase kernels.  Rounds
+// alternate the lift as listed (Alg. 3); between rounds the host ranks the
+// candidates (sum over graphs of the candidate's best cut) and replaces the
+// bottom half by perturbed copies of the top half.  From a lift's second
+// round on, the phase and its bookkeeping are replayed from a captured CUDA
+// graph; only the new step sizes / budgets and the starting block are
+// written before each replay.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "api_util.cuh"
+#include "deco_internal.cuh"
+#include "phase.cuh"
+
+using namespace deco;
+
+struct deco_batch {
+  deco_graph* U = nullptr;            // union graph
+  int32_t n_graphs = 0;
+  std::vector<int32_t> h_goff;        // first row of every graph (n_graphs + 1)
+  std::vector<int64_t> s1, s2;        // degree power sums per graph (IDI thresholds)
+  int32_t* gid = nullptr;             // device, row -> graph
+  int32_t* goff = nullptr;            // device, n_graphs + 1
+};
+
+namespace {
+
+// ---- host Philox4x32-10 (same definition as the device version)
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    const uint32_t n3 = (uint32_t)p0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+double u01_host(uint32_t x) { return (2.0 * (double)(x >> 9) + 1.0) * 5.9604644775390625e-8; }
+
+// ---- per-graph bookkeeping kernels
+constexpr int GCUT_ROWS = 32;   // rows per warp
+
+__global__ void k_cut_graphs(int32_t n, int32_t B, int32_t W, const int32_t* row_ptr, const int32_t* col_idx,
+                             const int32_t* wint, const uint32_t* zbits, const int32_t* gid, int64_t* cuts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int32_t k = blockIdx.y;
+  const int64_t r0 = warp * GCUT_ROWS;
+  if (r0 >= n) return;
+  const int32_t r1 = (int32_t)std::min<int64_t>(n, r0 + GCUT_ROWS);
+  const int32_t b = k * 32 + lane;
+  long long acc = 0;
+  int32_t cg = gid[r0];
+  for (int32_t v = (int32_t)r0; v < r1; ++v) {
+    const int32_t g = gid[v];
+    if (g != cg) {
+      if (b < B && acc) atomicAdd(reinterpret_cast<unsigned long long*>(cuts + (size_t)cg * B + b), (unsigned long long)acc);
+      acc = 0;
+      cg = g;
+    }
+    const uint32_t zv = zbits[(size_t)v * W + k];
+    int32_t racc = 0;
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      const int32_t u = col_idx[e];
+      if (u <= v) continue;
+      const uint32_t x = (zv ^ zbits[(size_t)u * W + k]) >> lane & 1u;
+      racc += wint ? (int32_t)x * wint[e] : (int32_t)x;
+    }
+    acc += racc;
+  }
+  if (b < B && acc) atomicAdd(reinterpret_cast<unsigned long long*>(cuts + (size_t)cg * B + b), (unsigned long long)acc);
+}
+
+// one block per graph: lowest index among the maximal cuts
+__global__ void k_argmax_graphs(int32_t B, const int64_t* cuts, int32_t* best) {
+  __shared__ long long sv[256];
+  __shared__ int32_t si[256];
+  const int32_t g = blockIdx.x;
+  long long bv = LLONG_MIN;
+  int32_t bi = INT32_MAX;
+  for (int32_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const long long c = cuts[(size_t)g * B + b];
+    if (c > bv) { bv = c; bi = b; }
+  }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const long long ov = sv[threadIdx.x + s];
+      const int32_t oi = si[threadIdx.x + s];
+      if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = ov;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) best[g] = si[0];
+}
+
+// global best record per graph: strictly larger cuts replace it
+__global__ void k_record_graphs(int32_t n_graphs, int32_t B, const int64_t* cuts, const int32_t* best,
+                                const int32_t* round, long long* rec_cut, int32_t* rec_round, int32_t* improved) {
+  const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_graphs) return;
+  const long long c = cuts[(size_t)g * B + best[g]];
+  const bool up = c > rec_cut[g];
+  if (up) { rec_cut[g] = c; rec_round[g] = *round; }
+  improved[g] = up ? 1 : 0;
+}
+
+__global__ void k_extract_graphs(int32_t n, int32_t W, const uint32_t* zbits, const int32_t* gid,
+                                 const int32_t* best, const int32_t* improved, uint8_t* round_best_z,
+                                 uint8_t* best_z) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int32_t g = gid[v];
+  const int32_t b = best[g];
+  const uint8_t z = (uint8_t)((zbits[(size_t)v * W + (b >> 5)] >> (b & 31)) & 1u);
+  round_best_z[v] = z;
+  if (improved[g]) best_z[v] = z;
+}
+
+__global__ void k_fill_ll(int32_t n, long long v, long long* p) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+extern "C" int deco_create_batch(const deco_graph* const* graphs, int32_t n_graphs, deco_batch** out) {
+  clear_error();
+  if (!graphs || !out || n_graphs < 1) { set_error("need graphs, out and n_graphs >= 1"); return DECO_ERR_ARG; }
+  int64_t n = 0, nnz = 0;
+  bool weighted = false;
+  for (int32_t i = 0; i < n_graphs; ++i) {
+    if (!graphs[i]) { set_error("graph %d is NULL", i); return DECO_ERR_ARG; }
+    n += graphs[i]->n;
+    nnz += graphs[i]->nnz;
+    weighted = weighted || graphs[i]->weighted;
+  }
+  if (n >= INT32_MAX || nnz >= INT32_MAX) { set_error("the union is too large"); return DECO_ERR_ARG; }
+  std::vector<int32_t> rp((size_t)n + 1), ci((size_t)nnz);
+  std::vector<float> w(weighted ? (size_t)nnz : 0);
+  std::unique_ptr<deco_batch> b(new deco_batch());
+  b->n_graphs = n_graphs;
+  b->h_goff.resize(n_graphs + 1);
+  int64_t ro = 0, eo = 0;
+  for (int32_t i = 0; i < n_graphs; ++i) {
+    const deco_graph* g = graphs[i];
+    b->h_goff[i] = (int32_t)ro;
+    b->s1.push_back(g->deg_s1);
+    b->s2.push_back(g->deg_s2);
+    for (int32_t v = 0; v < g->n; ++v) rp[ro + v] = (int32_t)(eo + g->h_row_ptr[v]);
+    for (int64_t e = 0; e < g->nnz; ++e) {
+      ci[eo + e] = (int32_t)(g->h_col[e] + ro);
+      if (weighted) w[eo + e] = g->weighted ? g->h_w[e] : 1.0f;
+    }
+    ro += g->n;
+    eo += g->nnz;
+  }
+  rp[n] = (int32_t)nnz;
+  b->h_goff[n_graphs] = (int32_t)n;
+  // every component was validated when it was created; rows of a +-1 graph are
+  // already in device order (positives first) and stay so
+  int rc = create_graph_impl((int32_t)n, nnz, rp.data(), ci.data(), weighted ? w.data() : nullptr,
+                             DECO_GRAPH_SKIP_SYMMETRY_CHECK, true, &b->U);
+  if (rc) return rc;
+  std::vector<int32_t> gid((size_t)n);
+  for (int32_t i = 0; i < n_graphs; ++i)
+    for (int32_t v = b->h_goff[i]; v < b->h_goff[i + 1]; ++v) gid[v] = i;
+  cudaError_t e = cudaMalloc((void**)&b->gid, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemcpy(b->gid, gid.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->goff, sizeof(int32_t) * (size_t)(n_graphs + 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->goff, b->h_goff.data(), sizeof(int32_t) * (size_t)(n_graphs + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->gid);
+    cudaFree(b->goff);
+    deco_destroy_graph(b->U);
+    return cuda_fail(e, "batch upload");
+  }
+  *out = b.release();
+  return DECO_OK;
+}
+
+extern "C" void deco_destroy_batch(deco_batch* b) {
+  if (!b) return;
+  cudaFree(b->gid);
+  cudaFree(b->goff);
+  deco_destroy_graph(b->U);
+  delete b;
+}
+
+extern "C" int deco_batch_graph(const deco_batch* b, const deco_graph** out) {
+  clear_error();
+  if (!b || !out) { set_error("NULL argument"); return DECO_ERR_ARG; }
+  *out = b->U;
+  return DECO_OK;
+}
+
+extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_params* p, const deco_population* pop,
+                                uint64_t seed, int64_t* best_cuts, uint8_t* assignment, int64_t* round_cuts,
+                                int64_t* round_scores, float* final_e, int32_t* final_T, void* stream,
+                                deco_result* out) {
+  clear_error();
+  if (!b || !p || !pop || !best_cuts || !out) { set_error("NULL argument"); return DECO_ERR_ARG; }
+  int rc = check_prec(p->precision);
+  if (rc || (rc = check_obj(p->objective))) return rc;
+  const int32_t P = pop->candidates;
+  if (B < 1 || P < 1 || B % P || pop->rounds < 1 || pop->t_lo < 0 || pop->t_hi < pop->t_lo ||
+      !(pop->e_hi >= pop->e_lo) || pop->n_lifts < 1 || pop->n_lifts > 8) {
+    set_error("bad population (B=%d P=%d rounds=%d T=[%d,%d] e=[%g,%g] lifts=%d)", B, P, pop->rounds, pop->t_lo,
+              pop->t_hi, (double)pop->e_lo, (double)pop->e_hi, pop->n_lifts);
+    return DECO_ERR_ARG;
+  }
+  int32_t max_lift = 1;
+  for (int i = 0; i < pop->n_lifts; ++i) {
+    if (pop->lifts[i] < 1 || pop->lifts[i] > 64) { set_error("bad lift %d", pop->lifts[i]); return DECO_ERR_ARG; }
+    max_lift = std::max(max_lift, pop->lifts[i]);
+  }
+  if (p->init == DECO_INIT_EXPLICIT || p->init == DECO_INIT_MEAN) {
+    set_error("batched solves draw their own starts (UNIFORM, IDI, DUI or IDI_HALF_UNIFORM)");
+    return DECO_ERR_UNSUPPORTED;
+  }
+  if (p->precision == DECO_PREC_BF16 && p->polish_steps > 0) {
+    set_error("FP32 polish is not available in batched solves");
+    return DECO_ERR_UNSUPPORTED;
+  }
+  const deco_graph* U = b->U;
+  const int32_t n = U->n, G = b->n_graphs;
+  const int32_t Cmax = B * max_lift;
+  const int32_t ld = (Cmax + 63) / 64 * 64;
+  const int32_t W = (B + 31) / 32;
+  const size_t block_elems = (size_t)n * ld;
+  // The rounds are captured into CUDA graphs, which the legacy default stream
+  // does not allow: the solve runs on a private stream ordered after the
+  // caller's stream on entry and before it on exit.
+  cudaStream_t caller = as_stream(stream);
+  cudaStream_t st = nullptr;
+  cudaEvent_t order_ev = nullptr;
+  DECO_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s, caller;
+    cudaEvent_t* ev;
+    ~StreamGuard() {
+      if (*ev) {
+        cudaEventRecord(*ev, s);
+        cudaStreamWaitEvent(caller, *ev, 0);
+        cudaEventDestroy(*ev);
+      }
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } sguard{st, caller, &order_ev};
+  DECO_CUDA_TRY(cudaEventCreateWithFlags(&order_ev, cudaEventDisableTiming));
+  DECO_CUDA_TRY(cudaEventRecord(order_ev, caller));
+  DECO_CUDA_TRY(cudaStreamWaitEvent(st, order_ev, 0));
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+
+  // ---- initial population (Sec. 4.3): counter (k, 0, 0, STREAM_EVOLVE)
+  std::vector<double> e(P);
+  std::vector<int64_t> T(P);
+  for (int32_t k = 0; k < P; ++k) {
+    uint32_t c[4] = {(uint32_t)k, 0u, 0u, STREAM_EVOLVE};
+    philox_host(c, k0, k1);
+    e[k] = (double)pop->e_lo + ((double)pop->e_hi - (double)pop->e_lo) * u01_host(c[0]);
+    T[k] = pop->t_lo + (int64_t)(c[1] % (uint32_t)(pop->t_hi - pop->t_lo + 1));
+  }
+  std::vector<double> gthresh(G);
+  for (int32_t i = 0; i < G; ++i) {
+    deco_graph tmp;
+    tmp.n = b->h_goff[i + 1] - b->h_goff[i];
+    tmp.deg_s1 = b->s1[i];
+    tmp.deg_s2 = b->s2[i];
+    gthresh[i] = idi_threshold(&tmp, p->beta);
+  }
+
+  int64_t edge_updates = 0, kernels = 0;
+  float ms = 0.0f;
+  std::vector<long long> hrec(G);
+  {
+    Scratch s(st);
+    void* ybuf[2] = {nullptr, nullptr};
+    float* vbuf = nullptr;
+    uint32_t* zbits = nullptr;
+    int64_t* cuts = nullptr;
+    int32_t *best_idx = nullptr, *improved = nullptr, *rec_round = nullptr, *d_round = nullptr;
+    long long* rec_cut = nullptr;
+    uint8_t *rbz = nullptr, *bz = nullptr;
+    float *h = nullptr, *alpha_cols = nullptr;
+    int32_t* steps_cols = nullptr;
+    int8_t* side = nullptr;
+    double* d_thresh = nullptr;
+    int32_t* flag = nullptr;
+    const size_t esz = elem_size(p->precision);
+    if ((rc = s.alloc(&ybuf[0], block_elems * esz)) || (rc = s.alloc(&ybuf[1], block_elems * esz))) return rc;
+    DECO_CUDA_TRY(cudaMemsetAsync(ybuf[0], 0, block_elems * esz, st));
+    DECO_CUDA_TRY(cudaMemsetAsync(ybuf[1], 0, block_elems * esz, st));
+    if (pop->momentum != 0.0f && (rc = s.alloc(&vbuf, block_elems * sizeof(float)))) return rc;
+    if ((rc = s.alloc(&zbits, sizeof(uint32_t) * (size_t)n * W))) return rc;
+    if ((rc = s.alloc(&cuts, sizeof(int64_t) * (size_t)G * B))) return rc;
+    if ((rc = s.alloc(&best_idx, sizeof(int32_t) * G)) || (rc = s.alloc(&improved, sizeof(int32_t) * G)) ||
+        (rc = s.alloc(&rec_round, sizeof(int32_t) * G)) || (rc = s.alloc(&d_round, sizeof(int32_t))) ||
+        (rc = s.alloc(&rec_cut, sizeof(long long) * G)))
+      return rc;
+    if ((rc = s.alloc(&rbz, (size_t)n)) || (rc = s.alloc(&bz, (size_t)n))) return rc;
+    if ((rc = s.alloc(&h, sizeof(float) * n)) || (rc = s.alloc(&side, (size_t)n))) return rc;
+    if ((rc = s.alloc(&alpha_cols, sizeof(float) * Cmax)) || (rc = s.alloc(&steps_cols, sizeof(int32_t) * Cmax)))
+      return rc;
+    if ((rc = s.alloc(&d_thresh, sizeof(double) * G)) || (rc = s.alloc(&flag, sizeof(int32_t)))) return rc;
+    DECO_CUDA_TRY(cudaMemcpyAsync(d_thresh, gthresh.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    DECO_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+    k_fill_ll<<<(G + 255) / 256, 256, 0, st>>>(G, LLONG_MIN, rec_cut);
+    DECO_CUDA_TRY(cudaGetLastError());
+
+    // one phase runner (and one captured graph) per distinct lift
+    struct Lane {
+      int lift = 0;
+      PhaseRunner R;
+      int uses = 0;
+      int32_t cap_steps = -1;
+      cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<std::unique_ptr<Lane>> lanes;
+    struct Cleanup {
+      std::vector<std::unique_ptr<Lane>>* l;
+      cudaStream_t st;
+      ~Cleanup() {
+        for (auto& x : *l) {
+          if (x->exec) cudaGraphExecDestroy(x->exec);
+          x->R.release(st);
+        }
+      }
+    } cleanup{&lanes, st};
+    for (int i = 0; i < pop->n_lifts; ++i) {
+      bool have = false;
+      for (auto& x : lanes) have = have || x->lift == pop->lifts[i];
+      if (have) continue;
+      lanes.emplace_back(new Lane());
+      lanes.back()->lift = pop->lifts[i];
+      if ((rc = lanes.back()->R.prepare(U, B * pop->lifts[i], ld, p->precision, p->kernel, st))) return rc;
+    }
+
+    cudaEvent_t ev0, ev1;
+    DECO_CUDA_TRY(cudaEventCreate(&ev0));
+    DECO_CUDA_TRY(cudaEventCreate(&ev1));
+    struct EvGuard {
+      cudaEvent_t a, b;
+      ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evg{ev0, ev1};
+    DECO_CUDA_TRY(cudaEventRecord(ev0, st));
+
+    const int32_t per = B / P;
+    std::vector<float> h_alpha(Cmax);
+    std::vector<int32_t> h_steps(Cmax);
+    std::vector<int64_t> h_cuts((size_t)G * B);
+    for (int32_t r = 0; r < pop->rounds; ++r) {
+      const int32_t lift = pop->lifts[r % pop->n_lifts];
+      const int32_t C = B * lift;
+      int32_t tmax = 0;
+      for (int32_t c = 0; c < C; ++c) {
+        const int32_t k = (c / lift) / per;
+        h_alpha[c] = (float)std::pow(10.0, e[k]);
+        h_steps[c] = (int32_t)T[k];
+        tmax = std::max<int32_t>(tmax, (int32_t)T[k]);
+      }
+      DECO_CUDA_TRY(cudaMemcpyAsync(alpha_cols, h_alpha.data(), sizeof(float) * C, cudaMemcpyHostToDevice, st));
+      DECO_CUDA_TRY(cudaMemcpyAsync(steps_cols, h_steps.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, st));
+      DECO_CUDA_TRY(cudaMemcpyAsync(d_round, &r, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+
+      // starting block of this round
+      InitLaunch il{};
+      fill_init(il, U, B, lift, ld, p, seed, r);
+      il.y = ybuf[0];
+      il.gid = b->gid;
+      il.goff = b->goff;
+      if (r == 0) {
+        if (p->init == DECO_INIT_DUI) {
+          set_error("DUI is not available in batched solves");
+          return DECO_ERR_UNSUPPORTED;
+        }
+        if (p->init == DECO_INIT_IDI || p->init == DECO_INIT_IDI_HALF_UNIFORM) {
+          if ((rc = launch_idi_batch(U, 0.0, d_thresh, b->gid, b->goff, k0, k1, 0, h, side, st))) return rc;
+          kernels += 2;
+          il.mean = h;
+        }
+      } else {
+        il.init = DECO_INIT_MEAN;
+        il.mean_bits = rbz;
+      }
+      if ((rc = launch_init(il, st))) return rc;
+      kernels += 1;
+      if (vbuf) DECO_CUDA_TRY(cudaMemsetAsync(vbuf, 0, block_elems * sizeof(float), st));
+
+      Lane* L = nullptr;
+      for (auto& x : lanes) if (x->lift == lift) L = x.get();
+      const bool mom = vbuf != nullptr;
+      auto body = [&](int64_t* kc) -> int {
+        int cur = 0;
+        int e2 = L->R.run(ybuf, cur, vbuf, tmax, p->objective, 0.0f, pop->momentum, alpha_cols, steps_cols, mom,
+                          false, flag, st, kc);
+        if (e2) return e2;
+        if ((e2 = launch_pack(U, B, lift, ld, p->precision, ybuf[cur], zbits, st))) return e2;
+        cudaError_t ce = cudaMemsetAsync(cuts, 0, sizeof(int64_t) * (size_t)G * B, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "memset cuts");
+        dim3 grid((unsigned)((((int64_t)n + GCUT_ROWS - 1) / GCUT_ROWS + 7) / 8), (unsigned)W);
+        k_cut_graphs<<<grid, 256, 0, st>>>(n, B, W, U->row_ptr, U->col_idx, U->wint, zbits, b->gid, cuts);
+        k_argmax_graphs<<<G, 256, 0, st>>>(B, cuts, best_idx);
+        k_record_graphs<<<(G + 127) / 128, 128, 0, st>>>(G, B, cuts, best_idx, d_round, rec_cut, rec_round, improved);
+        k_extract_graphs<<<(n + 255) / 256, 256, 0, st>>>(n, W, zbits, b->gid, best_idx, improved, rbz, bz);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return cuda_fail(ce, "batch bookkeeping");
+        if (kc) *kc += 5;
+        return DECO_OK;
+      };
+      // the phase length is part of the captured graph: capture again when the
+      // longest budget of this round differs from the captured one
+      if (L->uses >= 1 && L->R.plan.col_slabs <= 1) {
+        if (!L->exec || L->cap_steps != tmax) {
+          if (L->exec) cudaGraphExecDestroy(L->exec);
+          L->exec = nullptr;
+          L->cap_steps = tmax;
+          cudaGraph_t graph = nullptr;
+          DECO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          int64_t kc = 0;
+          const int brc = body(&kc);
+          cudaError_t ce = cudaStreamEndCapture(st, &graph);
+          if (brc) { if (graph) cudaGraphDestroy(graph); return brc; }
+          if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+          ce = cudaGraphInstantiate(&L->exec, graph, 0);
+          cudaGraphDestroy(graph);
+          if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        DECO_CUDA_TRY(cudaGraphLaunch(L->exec, st));
+        kernels += (int64_t)(L->R.plan.kernel == KERNEL_ONCHIP ? 1 : tmax) + 5;
+      } else {
+        if ((rc = body(&kernels))) return rc;
+      }
+      L->uses += 1;
+      edge_updates += U->nnz * (int64_t)C * tmax;   // every column is swept for the longest budget
+
+      // ---- rank, record, evolve (host, FP64)
+      DECO_CUDA_TRY(cudaMemcpyAsync(h_cuts.data(), cuts, sizeof(int64_t) * (size_t)G * B, cudaMemcpyDeviceToHost, st));
+      DECO_CUDA_TRY(cudaStreamSynchronize(st));
+      if (round_cuts) std::copy(h_cuts.begin(), h_cuts.end(), round_cuts + (size_t)r * G * B);
+      std::vector<long long> score(P, 0);
+      for (int32_t k = 0; k < P; ++k)
+        for (int32_t g = 0; g < G; ++g) {
+          long long m = LLONG_MIN;
+          for (int32_t j = k * per; j < (k + 1) * per; ++j) m = std::max<long long>(m, h_cuts[(size_t)g * B + j]);
+          score[k] += m;
+        }
+      if (round_scores) for (int32_t k = 0; k < P; ++k) round_scores[(size_t)r * P + k] = score[k];
+      if (r + 1 < pop->rounds) {
+        std::vector<int32_t> order(P);
+        for (int32_t k = 0; k < P; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return score[a] > score[c]; });
+        const int32_t nkeep = P / 2;
+        std::vector<double> ne = e;
+        std::vector<int64_t> nT = T;
+        const int32_t nrep = P - nkeep;
+        for (int32_t j = 0; j < nrep; ++j) {
+          const int32_t victim = order[P - 1 - j];
+          const int32_t src = order[nkeep > 0 ? j % nkeep : 0];
+          uint32_t c[4] = {(uint32_t)j, (uint32_t)r, 1u, STREAM_EVOLVE};
+          philox_host(c, k0, k1);
+          const double kPi = 3.141592653589793;
+          const double eps = std::sqrt(-2.0 * std::log(u01_host(c[0]))) * std::cos(2.0 * kPi * u01_host(c[1]));
+          const double epsp = u01_host(c[2]);
+          ne[victim] = std::min(std::max(e[src] + 0.2 * eps, (double)pop->e_lo), (double)pop->e_hi);
+          const int64_t t = (int64_t)std::floor((double)T[src] * (1.0 + 0.2 * (2.0 * epsp - 1.0)));
+          nT[victim] = std::min<int64_t>(std::max<int64_t>(t, pop->t_lo), pop->t_hi);
+        }
+        e = ne;
+        T = nT;
+      }
+    }
+    DECO_CUDA_TRY(cudaEventRecord(ev1, st));
+    int32_t hflag = 0;
+    DECO_CUDA_TRY(cudaMemcpyAsync(hrec.data(), rec_cut, sizeof(long long) * G, cudaMemcpyDeviceToHost, st));
+    DECO_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (assignment) DECO_CUDA_TRY(cudaMemcpyAsync(assignment, bz, (size_t)n, cudaMemcpyDeviceToHost, st));
+    DECO_CUDA_TRY(cudaStreamSynchronize(st));
+    DECO_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+    if (hflag & 2) { set_error("a bounded device wait of the on-chip kernel gave up"); return DECO_ERR_TIMEOUT; }
+    if (hflag) { set_error("a non-finite value appeared in the iterate"); return DECO_ERR_NONFINITE; }
+  }
+  long long total = 0;
+  for (int32_t g = 0; g < G; ++g) {
+    best_cuts[g] = hrec[g];
+    total += hrec[g];
+  }
+  if (final_e) for (int32_t k = 0; k < P; ++k) final_e[k] = (float)e[k];
+  if (final_T) for (int32_t k = 0; k < P; ++k) final_T[k] = (int32_t)T[k];
+  out->best_cut = total;
+  out->best_init = -1;
+  out->best_phase = -1;
+  out->edge_updates = edge_updates;
+  out->device_ms = ms;
+  out->kernel_launches = kernels;
+  return DECO_OK;
+}

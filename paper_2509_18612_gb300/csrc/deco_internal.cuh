@@ -169,13 +169,32 @@ struct InitLaunch {
   const uint8_t* mean_bits;   // n bytes z* (mean = 2z-1) instead of `mean`
   const float* x0;            // explicit start (ld stride)
   void* y;
+  const int32_t* gid;         // batch: graph of every row (null for one graph)
+  const int32_t* goff;        // batch: first row of every graph
 };
+
+// Key and row index of the counter-based draws of row v of a batch: graph i
+// draws with key (seed + i) and counts its own rows from 0.
+__device__ __forceinline__ void batch_key(const int32_t* gid, const int32_t* goff, int32_t v, uint32_t& k0,
+                                          uint32_t& k1, uint32_t& vr) {
+  const int32_t g = gid[v];
+  const uint64_t s = (((uint64_t)k1 << 32) | (uint64_t)k0) + (uint64_t)g;
+  k0 = (uint32_t)s;
+  k1 = (uint32_t)(s >> 32);
+  vr = (uint32_t)(v - goff[g]);
+}
 int launch_init(const InitLaunch& p, cudaStream_t st);
 int launch_idi(const deco_graph* g, double thresh, uint32_t k0, uint32_t k1, int32_t phase,
                float* h, int8_t* side_scratch, cudaStream_t st);
+int launch_idi_batch(const deco_graph* g, double thresh, const double* gthresh, const int32_t* gid,
+                     const int32_t* goff, uint32_t k0, uint32_t k1, int32_t phase, float* h,
+                     int8_t* side_scratch, cudaStream_t st);
 int launch_dui(const deco_graph* g, uint32_t k0, uint32_t k1, int32_t phase, float* h,
                cudaStream_t st);
 
 double idi_threshold(const deco_graph* g, float beta);
+
+int create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                      const float* weights, uint32_t flags, bool device_order, deco_graph** out);
 
 }  // namespace deco

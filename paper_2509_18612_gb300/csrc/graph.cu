@@ -65,6 +65,13 @@ extern "C" int deco_abi_version(void) { return DECO_ABI_VERSION; }
 extern "C" int deco_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr,
                                  const int32_t* col_idx, const float* weights, uint32_t flags,
                                  deco_graph** out) {
+  return deco::create_graph_impl(n, nnz, row_ptr, col_idx, weights, flags, false, out);
+}
+
+// `device_order`: the rows come from validated graphs in device edge order
+// (a +-1 row lists its positive entries first), so sortedness is not checked.
+int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                            const float* weights, uint32_t flags, bool device_order, deco_graph** out) {
   clear_error();
   if (!out) { set_error("out is NULL"); return DECO_ERR_ARG; }
   if (n < 1) { set_error("n must be >= 1 (got %d)", n); return DECO_ERR_ARG; }
@@ -90,7 +97,7 @@ extern "C" int deco_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr,
       int32_t u = col_idx[e];
       if (u < 0 || u >= n) { set_error("col_idx[%d] = %d out of range (row %d)", e, u, v); return DECO_ERR_GRAPH; }
       if (u == v) { set_error("self loop at row %d", v); return DECO_ERR_GRAPH; }
-      if (e > row_ptr[v] && col_idx[e - 1] >= u) {
+      if (!device_order && e > row_ptr[v] && col_idx[e - 1] >= u) {
         set_error("row %d: column indices not strictly increasing at entry %d", v, e);
         return DECO_ERR_GRAPH;
       }

@@ -29,8 +29,9 @@ __global__ void k_init(InitLaunch p) {
     store_y<PREC>(p.y, o, p.objective == DECO_OBJ_MULTILINEAR01 ? 2.0f * x - 1.0f : x);
     return;
   }
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)c, (uint32_t)p.phase, STREAM_INIT),
-                                p.k0, p.k1);
+  uint32_t k0 = p.k0, k1 = p.k1, vr = (uint32_t)v;
+  if (p.gid) batch_key(p.gid, p.goff, v, k0, k1, vr);   // graph i of a batch: key seed + i, own rows
+  const uint4 r = philox4x32_10(make_uint4(vr, (uint32_t)c, (uint32_t)p.phase, STREAM_INIT), k0, k1);
   bool gaussian = p.init != DECO_INIT_UNIFORM;
   float half = p.uniform_half_width;
   if (p.init == DECO_INIT_IDI_HALF_UNIFORM && (c / p.lift) >= p.B / 2) {
@@ -52,14 +53,21 @@ __global__ void k_init(InitLaunch p) {
 }
 
 // IDI stage 1: side of every important node (p_i ~ U{-1,1}), 0 elsewhere.
-__global__ void k_idi_sides(int32_t n, const int32_t* deg, double thresh, uint32_t k0, uint32_t k1,
+// A batch passes the row -> graph map and one threshold per graph.
+__global__ void k_idi_sides(int32_t n, const int32_t* deg, double thresh, const double* gthresh,
+                            const int32_t* gid, const int32_t* goff, uint32_t k0, uint32_t k1,
                             int32_t phase, int8_t* side) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
+  uint32_t vr = (uint32_t)v;
+  if (gid) {
+    thresh = gthresh[gid[v]];
+    batch_key(gid, goff, v, k0, k1, vr);
+  }
   const bool imp = (double)deg[v] > thresh;
   int8_t s = 0;
   if (imp) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)v, 0u, (uint32_t)phase, STREAM_IDI), k0, k1);
+    const uint4 r = philox4x32_10(make_uint4(vr, 0u, (uint32_t)phase, STREAM_IDI), k0, k1);
     s = (r.z & 1u) ? 1 : -1;
   }
   side[v] = s;
@@ -67,10 +75,12 @@ __global__ void k_idi_sides(int32_t n, const int32_t* deg, double thresh, uint32
 
 // IDI stage 2: unimportant nodes compare (A a)_i with (A b)_i (integers).
 __global__ void k_idi_mean(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
-                           const int32_t* wint, const int8_t* side, uint32_t k0, uint32_t k1,
-                           int32_t phase, float* h) {
+                           const int32_t* wint, const int8_t* side, const int32_t* gid, const int32_t* goff,
+                           uint32_t k0, uint32_t k1, int32_t phase, float* h) {
   const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
+  uint32_t vr = (uint32_t)v;
+  if (gid) batch_key(gid, goff, v, k0, k1, vr);
   const int8_t s = side[v];
   if (s != 0) { h[v] = (float)s; return; }
   long long aa = 0, ab = 0;
@@ -84,7 +94,7 @@ __global__ void k_idi_mean(int32_t n, const int32_t* row_ptr, const int32_t* col
   if (aa < ab) out = 1.0f;
   else if (aa > ab) out = -1.0f;
   else {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)v, 0u, (uint32_t)phase, STREAM_IDI), k0, k1);
+    const uint4 r = philox4x32_10(make_uint4(vr, 0u, (uint32_t)phase, STREAM_IDI), k0, k1);
     out = (r.w & 1u) ? 1.0f : -1.0f;
   }
   h[v] = out;
@@ -114,10 +124,17 @@ int launch_init(const InitLaunch& p, cudaStream_t st) {
 
 int launch_idi(const deco_graph* g, double thresh, uint32_t k0, uint32_t k1, int32_t phase,
                float* h, int8_t* side_scratch, cudaStream_t st) {
+  return launch_idi_batch(g, thresh, nullptr, nullptr, nullptr, k0, k1, phase, h, side_scratch, st);
+}
+
+int launch_idi_batch(const deco_graph* g, double thresh, const double* gthresh, const int32_t* gid,
+                     const int32_t* goff, uint32_t k0, uint32_t k1, int32_t phase, float* h,
+                     int8_t* side_scratch, cudaStream_t st) {
   const int block = 256;
   const unsigned grid = (unsigned)((g->n + block - 1) / block);
-  k_idi_sides<<<grid, block, 0, st>>>(g->n, g->deg, thresh, k0, k1, phase, side_scratch);
-  k_idi_mean<<<grid, block, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->wint, side_scratch, k0, k1, phase, h);
+  k_idi_sides<<<grid, block, 0, st>>>(g->n, g->deg, thresh, gthresh, gid, goff, k0, k1, phase, side_scratch);
+  k_idi_mean<<<grid, block, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->wint, side_scratch, gid, goff, k0, k1,
+                                     phase, h);
   DECO_CUDA_TRY(cudaGetLastError());
   return DECO_OK;
 }

@@ -463,6 +463,59 @@ def test_column_slab_schedule_bitwise_equals_global(name, precision, s):
         assert torch.equal(got[0][:, C:], y[:, C:])   # padding columns untouched
 
 
+# ------------------------------------------------------ batch + population
+
+def _batch_case():
+    graphs = [gg.ba_graph(n, 4, 30 + i) for i, n in enumerate([60, 90, 120, 75, 200])]
+    graphs.append(gg.torus_graph(8, 6, 3))            # a +-1 graph in the same batch
+    return graphs
+
+
+@pytest.mark.parametrize("kernel", [deco.DECO_KERNEL_GLOBAL, deco.DECO_KERNEL_ONCHIP])
+def test_batch_population_matches_oracle(kernel):
+    graphs = _batch_case()
+    handles = [deco.graph_from(g) for g in graphs]
+    batch = deco.deco_create_batch(handles)
+    B, P, rounds = 16, 4, 4
+    pop = deco.population(candidates=P, rounds=rounds, t_lo=30, t_hi=60, e_lo=-3.0, e_hi=-1.5, momentum=0.9,
+                          lifts=(1, 2))
+    p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM, kernel=kernel)
+    res, best, ex = deco.deco_solve_batch(batch, B, p, pop, 2024, want_assignment=True, want_round_cuts=True)
+    ref = O.solve_batch_population(graphs, B, P, rounds, [1, 2], 30, 60, -3.0, -1.5, 0.9,
+                                   O.Params(init="idi_half_uniform"), 2024)
+    for r in range(rounds):
+        agree = np.mean(ex["round_cuts"][r] == ref.round_cuts[r])
+        assert agree >= 0.99, (r, agree)
+        np.testing.assert_array_equal(ex["round_scores"][r], ref.round_scores[r])
+    np.testing.assert_array_equal(ex["final_T"], ref.final_T)
+    np.testing.assert_array_equal(ex["final_e"], ref.final_e.astype(np.float32))
+    assert list(best) == ref.best_cuts
+    # the returned assignment realises every graph's best cut
+    off = 0
+    for g, bc in zip(graphs, best):
+        assert O.cut_value(g, ex["assignment"][off:off + g.n]) == bc
+        off += g.n
+
+
+def test_batch_kernels_and_replay_agree():
+    graphs = _batch_case()
+    batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs])
+    pop = deco.population(candidates=4, rounds=5, t_lo=20, t_hi=20, e_lo=-2.5, e_hi=-1.5, lifts=(1, 2))
+    outs = []
+    for kernel in (deco.DECO_KERNEL_GLOBAL, deco.DECO_KERNEL_ONCHIP):
+        res, best, ex = deco.deco_solve_batch(batch, 16, deco.params(init=deco.DECO_INIT_IDI, kernel=kernel), pop, 5,
+                                              want_round_cuts=True)
+        outs.append((best.tolist(), ex["round_cuts"].tobytes(), ex["round_scores"].tobytes()))
+    assert outs[0] == outs[1]
+
+
+def test_batch_rejects_bad_population():
+    batch = deco.deco_create_batch([deco.graph_from(gg.ba_graph(50, 4, 1))])
+    with pytest.raises(deco.DecoError) as ei:
+        deco.deco_solve_batch(batch, 10, deco.params(), deco.population(candidates=4), 0)   # 10 % 4 != 0
+    assert ei.value.status == deco.DECO_ERR_ARG
+
+
 # ------------------------------------------------------------------ autotuner
 
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])

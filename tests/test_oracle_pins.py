@@ -400,6 +400,30 @@ def test_evolution_rules():
     assert ne[worst_first[0]] == -1.0 and ne[worst_first[1]] == -4.0
 
 
+def test_population_draws_in_range_and_batch_bookkeeping():
+    e, T = O.population_init(64, 500, 2000, -4.0, -1.0, 7)
+    assert np.all((e >= -4.0) & (e <= -1.0)) and np.all((T >= 500) & (T <= 2000))
+    assert len(set(T.tolist())) > 30 and np.std(e) > 0.5
+    eps, epsp = O.population_perturbations(1000, 3, 7)
+    assert abs(eps.mean()) < 0.1 and abs(eps.std() - 1.0) < 0.1 and 0.0 < epsp.min() and epsp.max() < 1.0
+    graphs = [gg.ba_graph(n, 4, s) for s, n in enumerate([40, 60, 50])]
+    res = O.solve_batch_population(graphs, 8, 4, 3, [1, 2], 20, 40, -3.0, -1.5, 0.9,
+                                   O.Params(init="idi_half_uniform"), 11)
+    for gi, g in enumerate(graphs):
+        # the best cut is the best over rounds and starts, never above the optimum
+        assert res.best_cuts[gi] == max(int(rc[gi].max()) for rc in res.round_cuts)
+        assert res.best_cuts[gi] * 2 >= g.m
+    for rc, sc in zip(res.round_cuts, res.round_scores):
+        for k in range(4):
+            assert sc[k] == sum(int(rc[gi, 2 * k:2 * k + 2].max()) for gi in range(3))
+    # rounds after the first use the evolved population
+    e1, T1 = res.populations[1]
+    keep = sorted(range(4), key=lambda k: (-res.round_scores[0][k], k))[:2]
+    e0, T0 = res.populations[0]
+    for k in keep:
+        assert e1[k] == e0[k] and T1[k] == T0[k]
+
+
 # -------------------------------------------------------------- solvers
 
 def test_solve_never_beats_brute_force_and_reports_consistently():
