@@ -383,6 +383,93 @@ def run_ba256():
             "round_best_score": [int(s.max()) for s in ex["round_scores"]]}
 
 
+LEARNED_BUDGETS = [25, 50, 100, 200, 400, 800, 1600, 3200]
+
+
+def run_learned():
+    """Learned proposal: a 3-layer message-passing network (hidden 64) trained
+    on the best assignments that the plain solver finds on 48 generated graphs
+    of the small-workload families (ER n ~ U{100..800}, p ~ U[0.01, 0.1];
+    BA n ~ U{100..800}, m = 4), then used as the mean of BF16 starts on unseen
+    BA(2000, 4) and ER(5000, 0.002) graphs with B = 256.
+
+    Time-to-target: the target is the best cut of a long plain FP32 run (IDI
+    starts, 4 x (1000 unlifted + 250 lifted) steps); each start method runs
+    pQUCO (momentum 0.9) with budgets T = 25, 50, ..., 3200 and reports the
+    first budget whose best cut is within 0.1 % of the target, with its device
+    time (the learned proposal's inference time included)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    rng = np.random.default_rng(5000)
+    train = []
+    for i in range(48):
+        n = int(rng.integers(100, 801))
+        train.append(gg.er_graph(n, float(rng.uniform(0.01, 0.1)), 5000 + i) if i % 2 == 0
+                     else gg.ba_graph(n, 4, 5000 + i))
+    handles = [deco.graph_from(g) for g in train]
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
+    a, b = ev()
+    a.record()
+    labels = []
+    for i, G in enumerate(handles):
+        _, z, _ = deco.deco_solve(G, 64, [(1, 300, 0.02, 0.9), (2, 100, 0.002, 0.9)],
+                                  deco.params(init=deco.DECO_INIT_IDI), 6000 + i, want_phase_cuts=False)
+        labels.append(z)
+    b.record()
+    torch.cuda.synchronize()
+    label_s = a.elapsed_time(b) / 1e3
+    batch = deco.deco_create_batch(handles)
+    zb = torch.from_numpy(np.concatenate(labels)).cuda()
+    model = deco.Mpnn(64, 3, 77)
+    a, b = ev()
+    a.record()
+    losses = model.train(batch, zb, steps=400, lr=3e-3, feat_seed=7)
+    b.record()
+    torch.cuda.synchronize()
+    train_s = a.elapsed_time(b) / 1e3
+
+    out = {"train_graphs": len(train), "label_s": label_s, "train_s": train_s, "train_steps": 400,
+           "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "eval": {}}
+    Bv = 256
+    for name, g in (("ba2000_m4", gg.ba_graph(2000, 4, 9001)), ("er5000_p0.002", gg.er_graph(5000, 0.002, 9002))):
+        G = deco.graph_from(g)
+        tres, _, _ = deco.deco_solve(G, Bv, [(1, 1000, 0.02, 0.9), (2, 250, 0.002, 0.9)] * 4,
+                                     deco.params(init=deco.DECO_INIT_IDI), 31337, want_phase_cuts=False)
+        target = tres.best_cut
+        h = torch.zeros(g.n, device="cuda")
+        model.infer(G, h, feat_seed=7, precision=deco.DECO_PREC_BF16)   # warm-up
+        methods = {
+            "learned_bf16": deco.params(init=deco.DECO_INIT_MEAN, precision=deco.DECO_PREC_BF16),
+            "idi_fp32": deco.params(init=deco.DECO_INIT_IDI),
+            "uniform_fp32": deco.params(init=deco.DECO_INIT_UNIFORM, uniform_half_width=1e-4),
+        }
+        res_m = {}
+        for mname, p in methods.items():
+            rec = {"reached": False, "budget": None, "device_s": None, "best_cut": None}
+            for T in LEARNED_BUDGETS:
+                torch.cuda.synchronize()
+                a, b = ev()
+                a.record()
+                if mname == "learned_bf16":
+                    model.infer(G, h, feat_seed=7, precision=deco.DECO_PREC_BF16)
+                    r, _, _ = deco.deco_solve(G, Bv, [(1, T, 0.02, 0.9)], p, 11, mean=h, want_phase_cuts=False)
+                else:
+                    r, _, _ = deco.deco_solve(G, Bv, [(1, T, 0.02, 0.9)], p, 11, want_phase_cuts=False)
+                b.record()
+                torch.cuda.synchronize()
+                rec.update(budget=T, device_s=a.elapsed_time(b) / 1e3, best_cut=int(r.best_cut))
+                if r.best_cut >= 0.999 * target:
+                    rec["reached"] = True
+                    break
+            res_m[mname] = rec
+        speed = None
+        if res_m["learned_bf16"]["reached"] and res_m["idi_fp32"]["reached"]:
+            speed = res_m["idi_fp32"]["device_s"] / res_m["learned_bf16"]["device_s"]
+        out["eval"][name] = {"n": g.n, "m": g.m, "target_cut": int(target), "methods": res_m,
+                             "speedup_learned_vs_idi": speed}
+    return out
+
+
 def profile_kernel(sel: int, precision: str, workload: str = "er800"):
     """Two phases of the dominant kernel with a fixed launch-shape selector,
     for ncu captures (capture the second launch).
@@ -458,6 +545,7 @@ def main():
     if rank == 0 and not args.main_only:
         extra["er1m_sparse"] = run_er1m()
         extra["ba256_population"] = run_ba256()
+        extra["learned_proposal"] = run_learned()
     if rank == 0:
         cpu = None
         if world == 1:

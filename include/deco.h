@@ -375,6 +375,49 @@ int deco_solve_batch(const deco_batch* b, int32_t B, const deco_params* p, const
                      uint64_t seed, int64_t* best_cuts, uint8_t* assignment, int64_t* round_cuts,
                      int64_t* round_scores, float* final_e, int32_t* final_T, void* stream, deco_result* out);
 
+/* ------------------------------------------------------ learned proposal
+ * A small message-passing network whose output h = tanh(o) in (-1,1)^n is
+ * used as the mean of the Gaussian starts (DECO_INIT_MEAN; Sec. 4.2 draws the
+ * starts around a mean vector, here a learned one instead of h_IDI).  The
+ * paper's method needs no training; this proposal is an optional start.
+ *   X  = [d/Delta, d/mean(d), 1/sqrt(d+1), five U(-1,1) features] per node
+ *        (features drawn with Philox, key feat_seed; graph i of a batch uses
+ *        feat_seed + i)
+ *   H0 = relu(X W0 + b0);  H_l = relu(H_{l-1} Ws_l + (D^-1 A H_{l-1}) Wn_l + b_l)
+ *   o  = H_L wo + bo;      loss per graph = min over (z, 1-z) of the mean
+ *        logistic loss softplus(-(2z-1) o); batch loss = mean over graphs.
+ * Parameters: one flat FP32 vector (W0, b0, [Ws, Wn, b] per layer, wo, bo),
+ * Xavier-uniform initialised from Philox (key seed). */
+typedef struct deco_mpnn deco_mpnn;
+
+int deco_mpnn_create(int32_t hidden, int32_t layers, uint64_t seed, deco_mpnn** out);
+void deco_mpnn_destroy(deco_mpnn* m);
+int deco_mpnn_num_params(const deco_mpnn* m, int64_t* count);
+/* host copies of the parameters; set also resets the Adam state */
+int deco_mpnn_get_params(const deco_mpnn* m, float* host, int64_t count);
+int deco_mpnn_set_params(deco_mpnn* m, const float* host, int64_t count);
+
+/* h (device, n floats) = tanh(o) for a graph, or for the union of a batch
+ * (exactly one of g and b non-NULL).  precision DECO_PREC_BF16 rounds the
+ * hidden activations to bfloat16 between layers. */
+int deco_mpnn_infer(const deco_mpnn* m, const deco_graph* g, const deco_batch* b, uint64_t feat_seed,
+                    int32_t precision, float* h, void* stream);
+
+/* Loss (host, FP64) and gradient (device, num_params floats, or NULL) for
+ * labels z (device, n bytes 0/1: the best assignments the solver found). */
+int deco_mpnn_loss_grad(const deco_mpnn* m, const deco_graph* g, const deco_batch* b, const uint8_t* z,
+                        uint64_t feat_seed, double* loss, float* grad, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias corrected) on the
+ * loss above; `loss` (host, or NULL) receives the loss before the step. */
+int deco_mpnn_train_step(deco_mpnn* m, const deco_graph* g, const deco_batch* b, const uint8_t* z,
+                         uint64_t feat_seed, float lr, double* loss, void* stream);
+
+/* `steps` Adam steps; losses (host, steps doubles, or NULL) receives the loss
+ * before every step (one copy after the last step). */
+int deco_mpnn_train(deco_mpnn* m, const deco_graph* g, const deco_batch* b, const uint8_t* z,
+                    uint64_t feat_seed, float lr, int32_t steps, double* losses, void* stream);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);
 

@@ -49,7 +49,9 @@ EXPORTED = [
     "deco_create_graph", "deco_destroy_graph", "deco_graph_info", "deco_eval_cut",
     "deco_eval_cuts", "deco_step", "deco_run_phase", "deco_run_phase_noalloc", "deco_round_cut",
     "deco_init_block", "deco_autotune", "deco_set_tuning", "deco_create_batch", "deco_destroy_batch",
-    "deco_batch_graph", "deco_solve_batch",
+    "deco_batch_graph", "deco_solve_batch", "deco_mpnn_create", "deco_mpnn_destroy", "deco_mpnn_num_params",
+    "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
+    "deco_mpnn_train_step", "deco_mpnn_train",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
 ]
 
@@ -114,6 +116,15 @@ def _load():
         "deco_batch_graph": (ctypes.c_int, [P, ctypes.POINTER(P)]),
         "deco_solve_batch": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_params), ctypes.POINTER(deco_population),
                                             U64, P, P, P, P, P, P, P, ctypes.POINTER(deco_result)]),
+        "deco_mpnn_create": (ctypes.c_int, [I32, I32, U64, ctypes.POINTER(P)]),
+        "deco_mpnn_destroy": (None, [P]),
+        "deco_mpnn_num_params": (ctypes.c_int, [P, P]),
+        "deco_mpnn_get_params": (ctypes.c_int, [P, P, I64]),
+        "deco_mpnn_set_params": (ctypes.c_int, [P, P, I64]),
+        "deco_mpnn_infer": (ctypes.c_int, [P, P, P, U64, I32, P, P]),
+        "deco_mpnn_loss_grad": (ctypes.c_int, [P, P, P, P, U64, P, P, P]),
+        "deco_mpnn_train_step": (ctypes.c_int, [P, P, P, P, U64, F32, P, P]),
+        "deco_mpnn_train": (ctypes.c_int, [P, P, P, P, U64, F32, I32, P, P]),
         "deco_round_cut": (ctypes.c_int, [P, I32, I32, I32, I32, P, P, P, P, P]),
         "deco_init_block": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(deco_params), U64, I32, P, P, P, P]),
         "deco_idi_mean": (ctypes.c_int, [P, F32, U64, I32, P, P]),
@@ -389,6 +400,68 @@ def deco_solve_batch(b: Batch, B: int, p: deco_params, pop: deco_population, see
                                 ctypes.byref(res)))
     return res, best, {"assignment": assignment, "round_cuts": rc, "round_scores": scores,
                        "final_e": fe, "final_T": fT}
+
+
+class Mpnn:
+    """Owning handle of the learned-proposal network (deco_mpnn)."""
+
+    def __init__(self, hidden: int = 64, layers: int = 3, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.deco_mpnn_create(int(hidden), int(layers), int(seed), ctypes.byref(h)))
+        self.handle = h.value
+        self.hidden, self.layers = hidden, layers
+        c = ctypes.c_int64()
+        _check(lib.deco_mpnn_num_params(self.handle, ctypes.byref(c)))
+        self.n_params = c.value
+
+    def close(self):
+        if self.handle:
+            lib.deco_mpnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib.deco_mpnn_get_params(self, _ptr(out), self.n_params))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib.deco_mpnn_set_params(self, _ptr(th), th.size))
+
+    def infer(self, target, h_dev, feat_seed: int = 0, precision: int = DECO_PREC_FP32, stream=None):
+        g, b = (target, None) if isinstance(target, Graph) else (None, target)
+        _check(lib.deco_mpnn_infer(self, g, b, int(feat_seed), int(precision), _ptr(h_dev), _stream(stream)))
+
+    def loss_grad(self, target, z_dev, grad_dev=None, feat_seed: int = 0, stream=None) -> float:
+        g, b = (target, None) if isinstance(target, Graph) else (None, target)
+        loss = ctypes.c_double()
+        _check(lib.deco_mpnn_loss_grad(self, g, b, _ptr(z_dev), int(feat_seed), ctypes.byref(loss),
+                                       _ptr(grad_dev), _stream(stream)))
+        return loss.value
+
+    def train_step(self, target, z_dev, lr: float = 1e-3, feat_seed: int = 0, stream=None) -> float:
+        g, b = (target, None) if isinstance(target, Graph) else (None, target)
+        loss = ctypes.c_double()
+        _check(lib.deco_mpnn_train_step(self, g, b, _ptr(z_dev), int(feat_seed), float(lr), ctypes.byref(loss),
+                                        _stream(stream)))
+        return loss.value
+
+    def train(self, target, z_dev, steps: int, lr: float = 1e-3, feat_seed: int = 0, stream=None) -> np.ndarray:
+        g, b = (target, None) if isinstance(target, Graph) else (None, target)
+        losses = np.zeros(max(int(steps), 1), dtype=np.float64)
+        _check(lib.deco_mpnn_train(self, g, b, _ptr(z_dev), int(feat_seed), float(lr), int(steps), _ptr(losses),
+                                   _stream(stream)))
+        return losses[:steps]
 
 
 def deco_abi_version() -> int:

@@ -32,7 +32,24 @@ struct deco_batch {
   std::vector<int64_t> s1, s2;        // degree power sums per graph (IDI thresholds)
   int32_t* gid = nullptr;             // device, row -> graph
   int32_t* goff = nullptr;            // device, n_graphs + 1
+  int32_t* gmax = nullptr;            // device, maximum degree per graph
+  double* gmean = nullptr;            // device, mean degree per graph
+  int32_t* gsize = nullptr;           // device, nodes per graph
 };
+
+namespace deco {
+int batch_feature_info(const deco_batch* b, const deco_graph** g, const int32_t** gid, const int32_t** goff,
+                       const int32_t** gmax, const double** gmean, const int32_t** gsize, int32_t* n_graphs) {
+  *g = b->U;
+  *gid = b->gid;
+  *goff = b->goff;
+  *gmax = b->gmax;
+  *gmean = b->gmean;
+  *gsize = b->gsize;
+  *n_graphs = b->n_graphs;
+  return DECO_OK;
+}
+}  // namespace deco
 
 namespace {
 
@@ -182,17 +199,30 @@ extern "C" int deco_create_batch(const deco_graph* const* graphs, int32_t n_grap
   int rc = create_graph_impl((int32_t)n, nnz, rp.data(), ci.data(), weighted ? w.data() : nullptr,
                              DECO_GRAPH_SKIP_SYMMETRY_CHECK, true, &b->U);
   if (rc) return rc;
-  std::vector<int32_t> gid((size_t)n);
-  for (int32_t i = 0; i < n_graphs; ++i)
+  std::vector<int32_t> gid((size_t)n), gmax(n_graphs), gsize(n_graphs);
+  std::vector<double> gmean(n_graphs);
+  for (int32_t i = 0; i < n_graphs; ++i) {
     for (int32_t v = b->h_goff[i]; v < b->h_goff[i + 1]; ++v) gid[v] = i;
-  cudaError_t e = cudaMalloc((void**)&b->gid, sizeof(int32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMemcpy(b->gid, gid.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->goff, sizeof(int32_t) * (size_t)(n_graphs + 1));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->goff, b->h_goff.data(), sizeof(int32_t) * (size_t)(n_graphs + 1), cudaMemcpyHostToDevice);
+    gmax[i] = graphs[i]->max_deg;
+    gsize[i] = graphs[i]->n;
+    gmean[i] = (double)graphs[i]->deg_s1 / (double)graphs[i]->n;
+  }
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e2 = cudaMalloc(dst, bytes);
+    if (e2 == cudaSuccess) e2 = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    return e2;
+  };
+  cudaError_t e = up((void**)&b->gid, gid.data(), sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = up((void**)&b->goff, b->h_goff.data(), sizeof(int32_t) * (size_t)(n_graphs + 1));
+  if (e == cudaSuccess) e = up((void**)&b->gmax, gmax.data(), sizeof(int32_t) * (size_t)n_graphs);
+  if (e == cudaSuccess) e = up((void**)&b->gsize, gsize.data(), sizeof(int32_t) * (size_t)n_graphs);
+  if (e == cudaSuccess) e = up((void**)&b->gmean, gmean.data(), sizeof(double) * (size_t)n_graphs);
   if (e != cudaSuccess) {
     cudaFree(b->gid);
     cudaFree(b->goff);
+    cudaFree(b->gmax);
+    cudaFree(b->gsize);
+    cudaFree(b->gmean);
     deco_destroy_graph(b->U);
     return cuda_fail(e, "batch upload");
   }
@@ -204,6 +234,9 @@ extern "C" void deco_destroy_batch(deco_batch* b) {
   if (!b) return;
   cudaFree(b->gid);
   cudaFree(b->goff);
+  cudaFree(b->gmax);
+  cudaFree(b->gsize);
+  cudaFree(b->gmean);
   deco_destroy_graph(b->U);
   delete b;
 }

@@ -7,44 +7,17 @@
 //
 // Layout: a group of G lanes owns one (row, column chunk); each lane owns one
 // 16-byte vector of the row (4 FP32 or 8 BF16 columns).  Every gathered
-// neighbour row segment is therefore read as G x 16 contiguous bytes.  The
-// neighbour loop is unrolled four ways so four independent gathers are in
-// flight per lane.  Used for graphs whose iterate does not fit on chip and as
-// the reference launch shape for the persistent kernels.
+// neighbour row segment is therefore read as G x 16 contiguous bytes; the
+// gather itself (spmm.cuh) keeps eight independent gathers in flight per
+// lane.  Used for graphs whose iterate does not fit on chip and as the
+// reference launch shape for the persistent kernels.
 #include <algorithm>
 
 #include "deco_internal.cuh"
+#include "spmm.cuh"
 
 namespace deco {
 namespace {
-
-template <int PREC>
-struct VecT;
-template <>
-struct VecT<DECO_PREC_FP32> {
-  static constexpr int N = 4;
-  __device__ static void load(const void* base, size_t idx, float* out) {
-    float4 q = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(base) + idx));
-    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
-  }
-  __device__ static void store(void* base, size_t idx, const float* in) {
-    *reinterpret_cast<float4*>(static_cast<float*>(base) + idx) = make_float4(in[0], in[1], in[2], in[3]);
-  }
-};
-template <>
-struct VecT<DECO_PREC_BF16> {
-  static constexpr int N = 8;
-  __device__ static void load(const void* base, size_t idx, float* out) {
-    uint4 q = __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + idx));
-    out[0] = bf16lo(q.x); out[1] = bf16hi(q.x); out[2] = bf16lo(q.y); out[3] = bf16hi(q.y);
-    out[4] = bf16lo(q.z); out[5] = bf16hi(q.z); out[6] = bf16lo(q.w); out[7] = bf16hi(q.w);
-  }
-  __device__ static void store(void* base, size_t idx, const float* in) {
-    uint4 q = make_uint4(pack_bf16x2(in[0], in[1]), pack_bf16x2(in[2], in[3]),
-                         pack_bf16x2(in[4], in[5]), pack_bf16x2(in[6], in[7]));
-    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + idx) = q;
-  }
-};
 
 struct KArgs {
   int32_t n, C, ld, G, nchunks;
@@ -65,21 +38,6 @@ struct KArgs {
   int32_t* flag;
 };
 
-template <int WMODE>
-__device__ __forceinline__ void edge_at(const KArgs& a, int32_t e, int32_t& j, float& wt) {
-  if (WMODE == W_UNIT) {
-    j = __ldg(a.col_idx + e);
-    wt = 1.0f;
-  } else if (WMODE == W_SIGN) {
-    uint32_t s = __ldg(a.col_sw + e);
-    j = (int32_t)(s & 0x7FFFFFFFu);
-    wt = (s & 0x80000000u) ? -1.0f : 1.0f;
-  } else {
-    j = __ldg(a.col_idx + e);
-    wt = __ldg(a.w + e);
-  }
-}
-
 template <int PREC, int WMODE, bool MOM, bool LAP>
 __global__ void __launch_bounds__(256) k_step_global(KArgs a) {
   using V = VecT<PREC>;
@@ -99,58 +57,8 @@ __global__ void __launch_bounds__(256) k_step_global(KArgs a) {
 #pragma unroll
   for (int k = 0; k < VN; ++k) acc[k] = 0.0f;
   const int32_t e0 = __ldg(a.row_ptr + r), e1 = __ldg(a.row_ptr + r + 1);
-  int32_t e = e0;
-  // eight independent gathers in flight per lane (raw 16-byte vectors, unpacked
-  // when accumulated); neighbours are still added in CSR order
-  for (; e + 8 <= e1; e += 8) {
-    int32_t j[8];
-    float wt[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) edge_at<WMODE>(a, e + q, j[q], wt[q]);
-    uint4 raw[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const size_t off = (size_t)j[q] * a.ld + c0;
-      raw[q] = PREC == DECO_PREC_FP32
-                   ? __ldg(reinterpret_cast<const uint4*>(static_cast<const float*>(a.yin) + off))
-                   : __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(a.yin) + off));
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float val[VN];
-      if (PREC == DECO_PREC_FP32) {
-        val[0] = __uint_as_float(raw[q].x); val[1] = __uint_as_float(raw[q].y);
-        val[2] = __uint_as_float(raw[q].z); val[3] = __uint_as_float(raw[q].w);
-      } else {
-        const uint32_t u[4] = {raw[q].x, raw[q].y, raw[q].z, raw[q].w};
-#pragma unroll
-        for (int h = 0; h < VN / 2; ++h) { val[2 * h] = bf16lo(u[h]); val[2 * h + 1] = bf16hi(u[h]); }
-      }
-#pragma unroll
-      for (int k = 0; k < VN; ++k) acc[k] = (WMODE == W_UNIT) ? acc[k] + val[k] : fmaf(wt[q], val[k], acc[k]);
-    }
-  }
-  for (; e + 4 <= e1; e += 4) {
-    int32_t j[4];
-    float wt[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) edge_at<WMODE>(a, e + q, j[q], wt[q]);
-    float val[4][VN];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) V::load(a.yin, (size_t)j[q] * a.ld + c0, val[q]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < VN; ++k) acc[k] = (WMODE == W_UNIT) ? acc[k] + val[q][k] : fmaf(wt[q], val[q][k], acc[k]);
-  }
-  for (; e < e1; ++e) {
-    int32_t j;
-    float wt, val[VN];
-    edge_at<WMODE>(a, e, j, wt);
-    V::load(a.yin, (size_t)j * a.ld + c0, val);
-#pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = (WMODE == W_UNIT) ? acc[k] + val[k] : fmaf(wt, val[k], acc[k]);
-  }
+  const CsrView A{a.col_idx, a.col_sw, a.w};
+  csr_gather_row<PREC, WMODE>(A, a.yin, a.ld, c0, e0, e1, acc);
 
   // ---- epilogue: gradient, momentum, step, projection
   const size_t base = (size_t)r * a.ld + c0;
