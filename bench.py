@@ -393,11 +393,12 @@ def run_learned():
     BA n ~ U{100..800}, m = 4), then used as the mean of BF16 starts on unseen
     BA(2000, 4) and ER(5000, 0.002) graphs with B = 256.
 
-    Time-to-target: the target is the best cut of a long plain FP32 run (IDI
-    starts, 4 x (1000 unlifted + 250 lifted) steps); each start method runs
-    pQUCO (momentum 0.9) with budgets T = 25, 50, ..., 3200 and reports the
-    first budget whose best cut is within 0.1 % of the target, with its device
-    time (the learned proposal's inference time included)."""
+    Time-to-target: the target is the best cut of a long plain FP32 pDECO run
+    (IDI starts, 4 x (1000 unlifted + 250 lifted) steps); each start method
+    runs the same pDECO structure, 2 x (T unlifted + T/4 lifted), momentum
+    0.9, with budgets T = 25, 50, ..., 3200 and reports the first budget whose
+    best cut is within 0.1 % of the target, with its device time (the learned
+    proposal's inference time included)."""
     import torch
     import paper_2509_18612_gb300 as deco
     rng = np.random.default_rng(5000)
@@ -450,11 +451,12 @@ def run_learned():
                 torch.cuda.synchronize()
                 a, b = ev()
                 a.record()
+                sched = [(1, T, 0.02, 0.9), (2, max(T // 4, 1), 0.002, 0.9)] * 2
                 if mname == "learned_bf16":
                     model.infer(G, h, feat_seed=7, precision=deco.DECO_PREC_BF16)
-                    r, _, _ = deco.deco_solve(G, Bv, [(1, T, 0.02, 0.9)], p, 11, mean=h, want_phase_cuts=False)
+                    r, _, _ = deco.deco_solve(G, Bv, sched, p, 11, mean=h, want_phase_cuts=False)
                 else:
-                    r, _, _ = deco.deco_solve(G, Bv, [(1, T, 0.02, 0.9)], p, 11, want_phase_cuts=False)
+                    r, _, _ = deco.deco_solve(G, Bv, sched, p, 11, want_phase_cuts=False)
                 b.record()
                 torch.cuda.synchronize()
                 rec.update(budget=T, device_s=a.elapsed_time(b) / 1e3, best_cut=int(r.best_cut))
