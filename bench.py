@@ -52,6 +52,9 @@ K_STEP_ER1M_TRAFFIC = 2013752064 + 248812288
 K_SLAB_ER800_TRAFFIC = 6756352
 
 
+DENSE_N, DENSE_P, DENSE_B, DENSE_STEPS, DENSE_ALPHA = 4096, 0.5, 128, 1000, 1e-4
+
+
 def er1m_graph():
     """Large sparse workload: ER with n = 10^6 and average degree 10."""
     return gg.er_graph_avg_degree(1_000_000, 10, 4)
@@ -349,6 +352,71 @@ def run_er1m():
                          "algorithmic_bytes_per_launch": alg}}
 
 
+def run_er4096_dense():
+    """Dense workload: ER(n = 4096, p = 0.5) (nnz ~ 8.4M), B = 128 BF16 starts
+    (IDI), one unlifted phase of T = 1000 steps (alpha = 1e-4, plain PGA);
+    rounding, cuts and argmax included.  Solved with the tensor-core kernel
+    (the autotuner's dense shape), with the sparse per-step kernel on the same
+    graph for comparison, and once in FP32 (sparse) for the precision's cut gap.
+
+    Roofline of its dominant kernel (k_dense_step), tensor-bound: algorithmic
+    FLOPs per step = 2 n^2 B (the dense product A Y, padding not counted),
+    timed as the difference of 250- and 50-step phases (CUDA events on the
+    launching stream), so the transposed copies in and out are excluded."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    g = gg.er_graph(DENSE_N, DENSE_P, DENSE_N)
+    G = deco.graph_from(g)
+    C = DENSE_B
+    BF, MUL = deco.DECO_PREC_BF16, deco.DECO_OBJ_MULTILINEAR01
+    sel, us_probe = deco.deco_autotune(G, C, BF, MUL, 0.0, 20)
+    dense_sel = sel if (sel & 0xFF) == deco.DECO_KERNEL_DENSE else deco.DECO_KERNEL_DENSE
+    sched = [(1, DENSE_STEPS, DENSE_ALPHA, 0.0)]
+
+    def solve(kernel, precision, seed=2):
+        p = deco.params(init=deco.DECO_INIT_IDI, precision=precision, kernel=kernel)
+        deco.deco_solve(G, C, [(1, 20, DENSE_ALPHA, 0.0)], p, 1, want_assignment=False, want_phase_cuts=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res, z, _ = deco.deco_solve(G, C, sched, p, seed, want_phase_cuts=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return res, z, e0.elapsed_time(e1) / 1e3
+
+    res_d, z_d, t_d = solve(dense_sel, BF)
+    res_s, _, t_s = solve(deco.DECO_KERNEL_GLOBAL, BF)
+    res_f, _, t_f = solve(deco.DECO_KERNEL_GLOBAL, deco.DECO_PREC_FP32)
+    # dominant kernel
+    y = (torch.rand(g.n, C, device="cuda") * 2e-4 - 1e-4).to(torch.bfloat16)
+    a = deco.step_args(MUL, BF, DENSE_ALPHA, 0.0)
+    deco.deco_run_phase(G, C, C, y, None, 4, a, dense_sel)
+    times = {}
+    for steps in (50, 250):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        deco.deco_run_phase(G, C, C, y, None, steps, a, dense_sel)
+        k1.record()
+        torch.cuda.synchronize()
+        times[steps] = k0.elapsed_time(k1) / 1e3
+    t_step = (times[250] - times[50]) / 200
+    flops = 2.0 * g.n * g.n * C
+    peaks, kind = measured_peaks()
+    ach = flops / t_step / 1e12
+    return {"workload": "ER(n=4096, p=0.5); B=128 bf16 starts (IDI); pQUCO T=1000, alpha=1e-4",
+            "value": res_d.edge_updates / t_d, "unit": "edge-updates/s", "solve_s": t_d,
+            "best_cut": res_d.best_cut, "m": g.m, "tuned_kernel": hex(sel), "dense_kernel": hex(dense_sel),
+            "autotune_us_per_step": us_probe, "gpu_launches": res_d.kernel_launches,
+            "sparse_same_graph": {"kernel": "global (bf16)", "value": res_s.edge_updates / t_s, "solve_s": t_s,
+                                  "best_cut": res_s.best_cut},
+            "fp32_sparse": {"value": res_f.edge_updates / t_f, "solve_s": t_f, "best_cut": res_f.best_cut,
+                            "cut_gap_bf16_dense_vs_fp32": (res_f.best_cut - res_d.best_cut) / res_f.best_cut},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_kind": kind + " (burst)",
+                         "kernel": "k_dense_step (one step)", "us_per_launch": t_step * 1e6,
+                         "algorithmic_flops_per_launch": flops}}
+
+
 def run_ba256():
     """Batched workload: 256 Barabasi-Albert graphs (n ~ U{200..1200}, m = 4),
     B = 256 starts each, population of 32 (alpha, T) candidates x 8 starts,
@@ -475,12 +543,15 @@ def run_learned():
 def profile_kernel(sel: int, precision: str, workload: str = "er800"):
     """Two phases of the dominant kernel with a fixed launch-shape selector,
     for ncu captures (capture the second launch).
-      er800: one 800-step unlifted phase of ER(800, 0.06), C = 1024, mu = 0.9
-      er1m:  two steps of ER(10^6, avg degree 10), C = 128, mu = 0"""
+      er800:  one 800-step unlifted phase of ER(800, 0.06), C = 1024, mu = 0.9
+      er1m:   two steps of ER(10^6, avg degree 10), C = 128, mu = 0
+      er4096: four steps of ER(4096, 0.5), C = 128, mu = 0"""
     import torch
     import paper_2509_18612_gb300 as deco
     if workload == "er1m":
         g, C, steps, mu = er1m_graph(), ER1M_B, 2, 0.0
+    elif workload == "er4096":
+        g, C, steps, mu = gg.er_graph(DENSE_N, DENSE_P, DENSE_N), DENSE_B, 4, 0.0
     else:
         g, C, steps, mu = graphs()[0], B, ROOF_STEPS, 0.9
     G = deco.graph_from(g)
@@ -505,7 +576,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", type=lambda s: int(s, 0), default=None,
                     help="run only the dominant kernel twice with this launch-shape selector")
-    ap.add_argument("--profile-workload", default="er800", choices=["er800", "er1m"])
+    ap.add_argument("--profile-workload", default="er800", choices=["er800", "er1m", "er4096"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -546,6 +617,7 @@ def main():
     extra = {}
     if rank == 0 and not args.main_only:
         extra["er1m_sparse"] = run_er1m()
+        extra["er4096_dense"] = run_er4096_dense()
         extra["ba256_population"] = run_ba256()
         extra["learned_proposal"] = run_learned()
     if rank == 0:

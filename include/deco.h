@@ -89,13 +89,27 @@ typedef enum deco_status {
  *  GLOBAL  always the per-step global-memory kernel
  *  ONCHIP  always the persistent on-chip kernel (DECO_ERR_UNSUPPORTED if it
  *          does not fit)
- * Both kernels perform the same FP32 operations in the same order, so their
- * iterates are bit-identical. */
+ *  DENSE   (BF16 blocks) the tensor-core kernel for dense graphs: A Y as a
+ *          dense BF16 x BF16 -> FP32 product on the 5th-generation tensor
+ *          cores (tcgen05, accumulator in tensor memory) with the update
+ *          fused into the epilogue; needs |w| <= 256, n <= 32768 and C <= 1024.
+ *          The dense copy of A (round_up(n,128)^2 BF16 values) is built on
+ *          first use and kept with the graph.  FP32 blocks (e.g. the FP32
+ *          polish of deco_solve) are planned as with AUTO.  Never chosen by
+ *          AUTO's cost model, only by the autotuner or explicitly.
+ * GLOBAL and ONCHIP perform the same FP32 operations in the same order, so
+ * their iterates are bit-identical.  DENSE sums each row of A Y in the
+ * tensor cores' order (and, with k > 1, k partial sums in rank order): its
+ * iterates agree with the others to FP32 summation error, and are
+ * reproducible from run to run. */
 #define DECO_KERNEL_AUTO 0
 #define DECO_KERNEL_GLOBAL 1
 #define DECO_KERNEL_ONCHIP 2
+#define DECO_KERNEL_DENSE 3
 /* With DECO_KERNEL_ONCHIP, DECO_KERNEL_CLUSTER(k) (k = 1, 2, 4 or 8) fixes the
- * cluster size instead of the built-in cost model's choice. */
+ * cluster size instead of the built-in cost model's choice.  With
+ * DECO_KERNEL_DENSE it fixes the split of the contraction over k CTAs of a
+ * cluster (k partial products reduced through distributed shared memory). */
 #define DECO_KERNEL_CLUSTER(k) ((k) << 8)
 /* With DECO_KERNEL_ONCHIP, fixes the CTA size of the on-chip kernel. */
 #define DECO_KERNEL_THREADS_512 (1 << 12)
@@ -191,21 +205,24 @@ int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void
  *  v       device n x ld float momentum, read at the start and written at the
  *          end (NULL when a->momentum == 0).
  *  a       step arguments; a->t is ignored (step t runs t = 0 .. steps-1).
- *  kernel  DECO_KERNEL_* (with the optional ONCHIP modifiers above).
+ *  kernel  DECO_KERNEL_* (with the optional modifiers above).
  *  nonfinite_flag  device int32 or NULL: bit 0 set if a new value is not
- *          finite; bit 1 set if a bounded wait of the on-chip kernel gave up
- *          (the block is then unreliable).
+ *          finite; bit 1 set if a bounded wait of the on-chip or dense kernel
+ *          gave up (the block is then unreliable).
  * Stream-ordered and asynchronous; scratch memory (exchange buffers, the
  * second block of the global kernel) is allocated and released in stream
  * order.  The first use of a graph with a given cluster size builds its
  * on-chip CSR image on the host (kept with the graph).
- * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED (ONCHIP does not fit), CUDA. */
+ * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED (ONCHIP does not fit, DENSE
+ * outside its limits), CUDA. */
 int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
                    const deco_step_args* a, int32_t kernel, int32_t* nonfinite_flag, void* stream);
 
 /* Autotuner: times every feasible launch shape of a phase on this graph --
- * the per-step global kernel and the on-chip kernel for each cluster size
- * (1, 2, 4, 8), CTA size (512, 1024) and exchange mode (DSMEM, L2) -- over
+ * the per-step global kernel, the on-chip kernel for each cluster size
+ * (1, 2, 4, 8), CTA size (512, 1024) and exchange mode (DSMEM, L2), and, for
+ * BF16 blocks of graphs with nnz >= n^2 / 64 inside the DENSE limits, the
+ * tensor-core kernel for each contraction split (1, 2, 4, 8) -- over
  * `probe_steps` steps of a C-column block with the given precision,
  * objective and momentum, and records the fastest with the graph.  Later
  * deco_solve / deco_run_phase calls with DECO_KERNEL_AUTO on a block of the
@@ -272,7 +289,7 @@ typedef struct deco_params {
   float scale;                /* down-scaling of Gaussian starts (paper: 1e-4) */
   float beta;                 /* IDI threshold (paper: 0.2) */
   float uniform_half_width;   /* DECO_INIT_UNIFORM half width (1 = full box) */
-  int32_t kernel;             /* DECO_KERNEL_* */
+  int32_t kernel;             /* DECO_KERNEL_* selector, modifiers included */
   int32_t reserved;
 } deco_params;
 

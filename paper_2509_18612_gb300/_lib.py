@@ -43,6 +43,7 @@ DECO_GRAPH_SKIP_SYMMETRY_CHECK = 0x1
 DECO_KERNEL_AUTO = 0
 DECO_KERNEL_GLOBAL = 1
 DECO_KERNEL_ONCHIP = 2
+DECO_KERNEL_DENSE = 3
 
 # every function include/deco.h declares (checked by the CPU test-suite)
 EXPORTED = [

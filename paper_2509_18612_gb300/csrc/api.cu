@@ -61,12 +61,7 @@ extern "C" int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* 
   if (rc) return rc;
   if (!y) { set_error("NULL block"); return DECO_ERR_ARG; }
   if (steps < 0) { set_error("steps must be >= 0"); return DECO_ERR_ARG; }
-  const int kind = kernel & 0xFF, want_k = (kernel >> 8) & 0xF, want_t = (kernel >> 12) & 0x3;
-  const int want_x = (kernel >> 14) & 0x3, want_s = (kernel >> 16) & 0xF;
-  if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_ONCHIP || (kernel & ~0xFFFFF) || want_t == 3 ||
-      want_x == 3 || ((want_k || want_t || want_x) && kind != DECO_KERNEL_ONCHIP) ||
-      (want_s && (kind != DECO_KERNEL_GLOBAL || want_s > 6)) ||
-      (want_k && ((want_k & (want_k - 1)) || want_k > 8))) {
+  if (!valid_selector(kernel)) {
     set_error("bad kernel selector 0x%x", kernel);
     return DECO_ERR_ARG;
   }
@@ -76,7 +71,7 @@ extern "C" int deco_run_phase(const deco_graph* g, int32_t C, int32_t ld, void* 
   if ((rc = R.prepare(g, C, ld, a->precision, kernel, st))) { R.release(st); return rc; }
   Scratch s(st);
   void* yb[2] = {y, nullptr};
-  if (R.plan.kernel != KERNEL_ONCHIP && steps > 0) {
+  if (R.plan.kernel == KERNEL_GLOBAL && steps > 0) {
     if ((rc = s.alloc(&yb[1], (size_t)g->n * ld * elem_size(a->precision)))) { R.release(st); return rc; }
   }
   int cur = 0;

@@ -20,17 +20,6 @@ __global__ void k_probe_fill(int64_t count, int prec, uint32_t seed, void* y) {
   else static_cast<float*>(y)[i] = v;
 }
 
-bool valid_selector(int kernel) {
-  const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
-  const int s = (kernel >> 16) & 0xF;
-  if (kernel & ~0xFFFFF) return false;
-  if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_ONCHIP || t == 3 || x == 3) return false;
-  if ((k || t || x) && kind != DECO_KERNEL_ONCHIP) return false;
-  if (s && (kind != DECO_KERNEL_GLOBAL || s > 6)) return false;
-  if (k && ((k & (k - 1)) || k > 8)) return false;
-  return true;
-}
-
 }  // namespace
 
 extern "C" int deco_set_tuning(const deco_graph* g, int32_t C, int32_t precision, int32_t kernel) {
@@ -66,6 +55,9 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
         if (k == 1 && x == 1) continue;   // a single CTA exchanges nothing
         cands.push_back(DECO_KERNEL_ONCHIP | (k << 8) | (t << 12) | (x << 14));
       }
+  // dense tensor-core kernel: BF16 blocks of graphs with at least n^2 / 64 entries
+  if (precision == DECO_PREC_BF16 && (double)g->nnz * 64.0 >= (double)g->n * (double)g->n)
+    for (int k = 1; k <= 8; k *= 2) cands.push_back(DECO_KERNEL_DENSE | (k << 8));
 
   float best_ms = -1.0f;
   int best = DECO_KERNEL_GLOBAL;

@@ -256,6 +256,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
   if (!b || !p || !pop || !best_cuts || !out) { set_error("NULL argument"); return DECO_ERR_ARG; }
   int rc = check_prec(p->precision);
   if (rc || (rc = check_obj(p->objective))) return rc;
+  if (!valid_selector(p->kernel)) { set_error("bad kernel selector 0x%x", p->kernel); return DECO_ERR_ARG; }
   const int32_t P = pop->candidates;
   if (B < 1 || P < 1 || B % P || pop->rounds < 1 || pop->t_lo < 0 || pop->t_hi < pop->t_lo ||
       !(pop->e_hi >= pop->e_lo) || pop->n_lifts < 1 || pop->n_lifts > 8) {
@@ -532,7 +533,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
     if (assignment) DECO_CUDA_TRY(cudaMemcpyAsync(assignment, bz, (size_t)n, cudaMemcpyDeviceToHost, st));
     DECO_CUDA_TRY(cudaStreamSynchronize(st));
     DECO_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
-    if (hflag & 2) { set_error("a bounded device wait of the on-chip kernel gave up"); return DECO_ERR_TIMEOUT; }
+    if (hflag & 2) { set_error("a bounded device wait of the on-chip or dense kernel gave up"); return DECO_ERR_TIMEOUT; }
     if (hflag) { set_error("a non-finite value appeared in the iterate"); return DECO_ERR_NONFINITE; }
   }
   long long total = 0;

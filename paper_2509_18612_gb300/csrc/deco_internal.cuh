@@ -51,6 +51,7 @@ struct deco_graph {
   int64_t nnz = 0;
   int weighted = 0;             // caller supplied weights
   int wmode = deco::W_UNIT;     // storage used by the kernels
+  int32_t max_abs_w = 1;        // largest |w|
   int device = 0;
   // host-side facts (degree statistics for IDI / DUI)
   int64_t deg_s1 = 0, deg_s2 = 0;
@@ -59,6 +60,8 @@ struct deco_graph {
   std::vector<int32_t> h_col;       // host copy of the device edge order
   std::vector<float> h_w;           // host copy of the device-order weights (or empty)
   std::vector<SlabImage> images;    // on-chip CSR images, one per cluster size used
+  __nv_bfloat16* dense = nullptr;   // dense BF16 copy of A for the tensor-core kernel (built on first use)
+  int32_t dense_ld = 0;             // its row stride, round_up(n, 128)
   struct Tuning {
     int32_t C, prec, kernel;
   };

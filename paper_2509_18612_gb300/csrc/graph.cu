@@ -44,6 +44,7 @@ double idi_threshold(const deco_graph* g, float beta) {
 static void free_graph(deco_graph* g) {
   if (!g) return;
   for (auto& im : g->images) cudaFree(im.data);
+  cudaFree(g->dense);
   cudaFree(g->row_ptr);
   cudaFree(g->col_idx);
   cudaFree(g->col_sw);
@@ -105,6 +106,7 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
   }
   // ---- weights: nonzero integers, |w| <= 2^20 (exact in FP32 sums and in int cut sums)
   bool all_unit = true, all_pm1 = true;
+  float max_abs_w = 1.0f;
   if (weights) {
     for (int64_t e = 0; e < nnz; ++e) {
       float x = weights[e];
@@ -121,6 +123,7 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
       }
       if (x != 1.0f) all_unit = false;
       if (x != 1.0f && x != -1.0f) all_pm1 = false;
+      max_abs_w = std::max(max_abs_w, std::fabs(x));
     }
   }
   // ---- symmetry: (u,v) present with the same weight as (v,u); binary search in row u
@@ -152,6 +155,7 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
   g->nnz = nnz;
   g->weighted = weights ? 1 : 0;
   g->wmode = (!weights || all_unit) ? W_UNIT : (all_pm1 ? W_SIGN : W_GENERAL);
+  g->max_abs_w = (int32_t)max_abs_w;
   cudaGetDevice(&g->device);
   g->h_row_ptr.assign(row_ptr, row_ptr + (size_t)n + 1);
   std::vector<int32_t> deg(n);

@@ -8,6 +8,7 @@
 
 #include "deco_internal.cuh"
 #include "phase.cuh"
+#include "dense_tc.cuh"
 #include "slab.cuh"
 
 namespace deco {
@@ -60,6 +61,18 @@ static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int wa
   return per_cta * waves;
 }
 
+bool valid_selector(int kernel) {
+  const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
+  const int s = (kernel >> 16) & 0xF;
+  if (kernel & ~0xFFFFF) return false;
+  if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_DENSE || t == 3 || x == 3) return false;
+  if ((t || x) && kind != DECO_KERNEL_ONCHIP) return false;
+  if (k && kind != DECO_KERNEL_ONCHIP && kind != DECO_KERNEL_DENSE) return false;
+  if (s && (kind != DECO_KERNEL_GLOBAL || s > 6)) return false;
+  if (k && ((k & (k - 1)) || k > 8)) return false;
+  return true;
+}
+
 static std::mutex g_image_mutex;
 
 int tuned_selector(const deco_graph* g, int32_t C, int prec) {
@@ -75,6 +88,33 @@ void record_tuning(const deco_graph* g, int32_t C, int prec, int kernel) {
   for (auto& t : tv)
     if (t.C == C && t.prec == prec) { t.kernel = kernel; return; }
   tv.push_back({C, prec, kernel});
+}
+
+// Dense tensor-core kernel: limits, padding and the contraction split (the
+// largest power of two <= 8 that keeps row tiles x column tiles x split within
+// one wave of the SMs, unless fixed by the caller).
+static int plan_dense(const deco_graph* g, int32_t C, int want_k, PhasePlan* plan) {
+  if (g->n < 1 || g->n > DENSE_MAX_N || C > DENSE_MAX_C || g->max_abs_w > DENSE_MAX_W) {
+    set_error("the dense kernel needs n <= %d, C <= %d and |w| <= %d (n=%d, C=%d, max |w|=%d)", DENSE_MAX_N,
+              DENSE_MAX_C, DENSE_MAX_W, g->n, C, g->max_abs_w);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  plan->kernel = KERNEL_DENSE;
+  plan->kpad = (g->n + DENSE_BM - 1) / DENSE_BM * DENSE_BM;
+  plan->cpad = (C + 31) / 32 * 32;
+  const int nk = plan->kpad / DENSE_BK;
+  const int64_t tiles = (int64_t)(plan->kpad / DENSE_BM) * ((plan->cpad + 255) / 256);
+  int ks = want_k;
+  if (!ks) {
+    ks = 1;
+    while (ks < 8 && 2 * ks <= nk && tiles * 2 * ks <= device_sm_count()) ks *= 2;
+  }
+  if (ks > nk) {
+    set_error("dense kernel: a split of %d exceeds the %d contraction chunks of n=%d", ks, nk, g->n);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  plan->ks = ks;
+  return DECO_OK;
 }
 
 int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, PhasePlan* plan) {
@@ -94,6 +134,11 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_x = (force >> 14) & 0x3;
   const int want_s = (force >> 16) & 0xF;
   force &= 0xFF;
+  if (force == DECO_KERNEL_DENSE) {
+    // BF16 blocks only; an FP32 block (e.g. the FP32 polish) is planned as AUTO
+    if (prec != DECO_PREC_BF16) return plan_phase(g, C, ld, prec, DECO_KERNEL_AUTO, plan);
+    return plan_dense(g, C, want_k, plan);
+  }
   plan->threads = want_t == 1 ? 512 : 1024;
   plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
   if (force == DECO_KERNEL_GLOBAL) {
@@ -157,6 +202,29 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
   prec = prec_;
   int rc = plan_phase(g, C, ld, prec, force, &plan);
   if (rc) return rc;
+  if (plan.kernel == KERNEL_DENSE) {
+    {
+      std::lock_guard<std::mutex> lock(g_image_mutex);
+      // the dense copy lives with the graph, like the on-chip CSR images
+      if (!g->dense) {
+        __nv_bfloat16* A = nullptr;
+        if ((rc = dense_build(g, plan.kpad, &A, st))) return rc;
+        const_cast<deco_graph*>(g)->dense = A;
+        const_cast<deco_graph*>(g)->dense_ld = plan.kpad;
+      }
+    }
+    const size_t elems = (size_t)plan.cpad * plan.kpad;
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaMallocAsync((void**)&yt[i], elems * 2, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(transposed block)");
+      // node padding of YT must stay zero (finite) for the products with A's zero columns
+      if ((e = cudaMemsetAsync(yt[i], 0, elems * 2, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    cudaError_t e = cudaMallocAsync((void**)&vt, elems * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(transposed momentum)");
+    if ((e = cudaMemsetAsync(vt, 0, elems * sizeof(float), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    return DECO_OK;
+  }
   if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
   {
     std::lock_guard<std::mutex> lock(g_image_mutex);
@@ -212,6 +280,48 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     int rc = launch_slab(p, plan.items, prec, g->wmode, st);
     if (rc) return rc;
     if (kernels) *kernels += 1;
+    return DECO_OK;
+  }
+  if (plan.kernel == KERNEL_DENSE) {
+    // transposed copy in, `steps` tensor-core steps ping-ponging yt[0] / yt[1], copy back
+    const bool momv = mu != 0.0f && v != nullptr;
+    const int32_t kpad = plan.kpad;
+    int rc = dense_to_t(y[cur], g->n, ld, C, yt[0], kpad, 2, st);
+    if (rc) return rc;
+    if (momv) {
+      if (load_v) rc = dense_to_t(v, g->n, ld, C, vt, kpad, 4, st);
+      else if (cudaError_t e = cudaMemsetAsync(vt, 0, sizeof(float) * (size_t)plan.cpad * kpad, st))
+        rc = cuda_fail(e, "memset");
+      if (rc) return rc;
+    }
+    DenseStep p{};
+    p.n = g->n;
+    p.kpad = kpad;
+    p.cpad = plan.cpad;
+    p.C = C;
+    p.ks = plan.ks;
+    p.objective = objective;
+    p.A = g->dense;
+    p.VT = momv ? vt : nullptr;
+    p.dnet = g->dnet;
+    const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
+    p.alpha = fac * alpha;
+    p.afac = fac;
+    p.mu = momv ? mu : 0.0f;
+    p.alpha_cols = alpha_cols;
+    p.steps_cols = steps_cols;
+    p.flag = flag;
+    int c = 0;
+    for (int32_t t = 0; t < steps; ++t) {
+      p.YT = yt[c];
+      p.YTout = yt[c ^ 1];
+      p.t = t;
+      if ((rc = launch_dense_step(p, st))) return rc;
+      c ^= 1;
+    }
+    if ((rc = dense_from_t(yt[c], kpad, C, y[cur], g->n, ld, 2, st))) return rc;
+    if (momv && store_v && (rc = dense_from_t(vt, kpad, C, v, g->n, ld, 4, st))) return rc;
+    if (kernels) *kernels += steps + 2 + (momv ? 1 + (store_v ? 1 : 0) : 0);
     return DECO_OK;
   }
   StepLaunch sl{};
@@ -287,6 +397,12 @@ void PhaseRunner::release(cudaStream_t st) {
   if (xbuf) cudaFreeAsync(xbuf, st);
   if (vslab) cudaFreeAsync(vslab, st);
   if (ypart) cudaFreeAsync(ypart, st);
+  for (auto& p : yt) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+  }
+  if (vt) cudaFreeAsync(vt, st);
+  vt = nullptr;
   xbuf = nullptr;
   vslab = nullptr;
   ypart = nullptr;

@@ -7,7 +7,7 @@
 
 namespace deco {
 
-enum KernelKind { KERNEL_GLOBAL = 0, KERNEL_ONCHIP = 1 };
+enum KernelKind { KERNEL_GLOBAL = 0, KERNEL_ONCHIP = 1, KERNEL_DENSE = 2 };
 
 struct PhasePlan {
   int kernel = KERNEL_GLOBAL;
@@ -19,9 +19,13 @@ struct PhasePlan {
   int items = 0;                 // column slabs
   int32_t max_own = 0, max_img_words = 0;
   SlabImage image;               // on-chip CSR image (owned by the graph)
+  int ks = 1;                    // dense kernel: contraction split over a cluster
+  int32_t kpad = 0, cpad = 0;    // dense kernel: padded n and C
 };
 
 int device_sm_count();
+// a well-formed DECO_KERNEL_* selector (kind and the modifiers it accepts)
+bool valid_selector(int kernel);
 // recorded launch shape for (C, prec) on g, or -1
 int tuned_selector(const deco_graph* g, int32_t C, int prec);
 void record_tuning(const deco_graph* g, int32_t C, int prec, int kernel);
@@ -36,11 +40,13 @@ struct PhaseRunner {
   unsigned char* xbuf = nullptr;  // exchange buffer of the on-chip kernel (k > 1)
   float* vslab = nullptr;         // slab-major momentum of the column-slab schedule
   unsigned char* ypart = nullptr; // slab-major ping-pong partner of the column-slab schedule
+  __nv_bfloat16* yt[2] = {nullptr, nullptr};   // dense kernel: transposed iterate pair
+  float* vt = nullptr;                         // dense kernel: transposed momentum
 
   // choose the kernel for a C-column block of g (builds the CSR image once)
   int prepare(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, cudaStream_t st);
   // `steps` steps on y[cur] (the global kernel ping-pongs y[0] / y[1] and
-  // updates cur; the on-chip kernel works in place)
+  // updates cur; the on-chip and dense kernels work in place)
   int run(void* y[2], int& cur, float* v, int32_t steps, int objective, float alpha, float mu,
           const float* alpha_cols, const int32_t* steps_cols, bool load_v, bool store_v, int32_t* flag,
           cudaStream_t st, int64_t* kernels);

@@ -47,7 +47,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
   if (!phases || !p || !out) { set_error("NULL argument"); return DECO_ERR_ARG; }
   if (B < 1 || n_phases < 1 || n_phases > 64) { set_error("need B >= 1 and 1 <= n_phases <= 64"); return DECO_ERR_ARG; }
   if ((rc = check_prec(p->precision)) || (rc = check_obj(p->objective))) return rc;
-  if (p->kernel < DECO_KERNEL_AUTO || p->kernel > DECO_KERNEL_ONCHIP) { set_error("bad kernel %d", p->kernel); return DECO_ERR_ARG; }
+  if (!valid_selector(p->kernel)) { set_error("bad kernel selector 0x%x", p->kernel); return DECO_ERR_ARG; }
   int32_t max_lift = 1;
   bool any_mom = false;
   for (int k = 0; k < n_phases; ++k) {
@@ -209,7 +209,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
     DECO_CUDA_TRY(cudaStreamSynchronize(st));
     DECO_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
     if (hflag & 2) {
-      set_error("a bounded device wait of the on-chip kernel gave up");
+      set_error("a bounded device wait of the on-chip or dense kernel gave up");
       return DECO_ERR_TIMEOUT;
     }
     if (hflag) {
