@@ -9,23 +9,25 @@
 // The iterate is kept transposed, YT = Y^T (cpad x kpad, node index
 // contiguous), so both MMA operands are K-major: the A tile is 128 nodes x 64
 // neighbour nodes, the B tile is N columns x the same 64 neighbour nodes of
-// YT.  Tiles are staged in shared memory in the no-swizzle K-major layout
-// (8-row x 16-byte core matrices, core (r/8, k/8) at (r/8) * 1024 + (k/8) *
-// 128 bytes) by cp.async through a four-stage ring; one thread issues the
-// MMAs (M = 128, N <= 256, K = 16 each) and commits every stage to an
-// mbarrier that frees it for the next load.
+// YT, each a stack of 128-byte rows in the 128-byte swizzled layout written by
+// TMA.  One lane issues the TMA loads of a stage ring, one lane issues the
+// MMAs (M = 128, N <= 256, K = 16 each); full / empty mbarriers hand the
+// stages between them, so no block barrier runs inside the contraction.
 //
-// Grid: (row tiles x ks) CTAs along x, column tiles of <= 256 along y.  The ks
-// CTAs of a cluster split the contraction of one 128 x N output tile; each
-// moves its partial product from tensor memory to shared memory, the cluster
-// synchronises, and CTA r reduces rows [r 128/ks, (r+1) 128/ks) over the ks
-// partials (rank order, through distributed shared memory) and applies the
-// update.  Every mbarrier wait is bounded (globaltimer); the accumulator's
-// tensor-memory columns are released on every path.
+// Grid: (row tiles x KS) CTAs along x, column tiles of <= 256 along y.  The KS
+// CTAs of a cluster split the contraction of one 128 x N output tile.  After
+// the contraction each CTA pushes the rows of its partial product owned by a
+// peer into that peer's shared memory (distributed shared memory stores), and
+// CTA r reduces rows [r 128/KS, (r+1) 128/KS) over the KS partials in rank
+// order and applies the update, eight rows of one column per 16-byte vector.
+// The y and V operands of the update are loaded into registers before the
+// contraction starts.  Every mbarrier wait is bounded (globaltimer); the
+// accumulator's tensor-memory columns are released on every path.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "dense_tc.cuh"
 
@@ -34,8 +36,16 @@ namespace cg = cooperative_groups;
 namespace deco {
 namespace {
 
-constexpr int BM = DENSE_BM, BK = DENSE_BK, STAGES = 4, NTHREADS = 128;
+constexpr int BM = DENSE_BM, BK = DENSE_BK, NTHREADS = 128, MAX_STAGES = 8, PF = 4;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait at most
+constexpr uint32_t RING_BUDGET = 200u * 1024u;
+
+struct DenseArgs {
+  CUtensorMap tmA;   // dense A, box 64 x 128
+  CUtensorMap tmY;   // YT of this step, box 64 x min(256, cpad)
+  DenseStep p;
+  int stages;
+};
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -67,24 +77,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
   return false;
 }
-
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Shared-memory matrix descriptor of the tcgen05 family: start address,
-// leading-dimension byte offset (between core matrices along K), stride byte
-// offset (between 8-row groups), all in 16-byte units; bit 46 set; base
-// offset 0; no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// 2-D tiled TMA load into this CTA's shared memory, completion counted on bar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of the tcgen05 family for a K-major operand
+// in the 128-byte swizzled layout: start address, leading byte offset (unused
+// for this layout, 16), stride byte offset 1024 (eight 128-byte rows), bit 46
+// set, base offset 0 (atoms are 1024-byte aligned), layout type 2.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -126,41 +143,57 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* out) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// One stage: A rows [m0, m0+128) x k [k0, k0+64) and YT rows [0, nt) x the
-// same k, each 16-byte chunk (row r, k-group q) at (r/8) 1024 + q 128 + (r%8) 16.
-__device__ __forceinline__ void load_stage(unsigned char* sA, unsigned char* sB, const __nv_bfloat16* A,
-                                           int32_t kpad, const __nv_bfloat16* YT, int m0, int k0, int nt,
-                                           int tid) {
-  for (int i = tid; i < BM * (BK / 8); i += NTHREADS) {
-    const int r = i >> 3, q = i & 7;
-    cp16(sA + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * kpad + k0 + q * 8);
-  }
-  for (int i = tid; i < nt * (BK / 8); i += NTHREADS) {
-    const int r = i >> 3, q = i & 7;
-    cp16(sB + (r >> 3) * 1024 + q * 128 + (r & 7) * 16, YT + (size_t)r * kpad + k0 + q * 8);
-  }
+__device__ __forceinline__ void unpack8(uint4 q, float* y) {
+  y[0] = bf16lo(q.x); y[1] = bf16hi(q.x); y[2] = bf16lo(q.y); y[3] = bf16hi(q.y);
+  y[4] = bf16lo(q.z); y[5] = bf16hi(q.z); y[6] = bf16lo(q.w); y[7] = bf16hi(q.w);
 }
 
-template <bool MOM, bool LAP>
-__global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(DenseStep p) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[STAGES + 1];
+template <bool MOM, bool LAP, int KS>
+__global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constant__ DenseArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], done;
   __shared__ uint32_t tmem_slot;
+  __shared__ int sh_issued, sh_consumed, sh_timeout;
+  const DenseStep& p = args.p;
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ks = p.ks;
   const int r = (int)cluster.block_rank();
-  const int m0 = (int)(blockIdx.x / ks) * BM;
+  const int m0 = (int)(blockIdx.x / KS) * BM;
   const int cbase = (int)blockIdx.y * 256;
   const int nt = min(256, p.cpad - cbase);   // MMA N of this column tile, a multiple of 32
-  const int ntmax = min(256, p.cpad);        // stage size is that of the widest tile
+  const int ntmax = min(256, p.cpad);        // rows of the YT box (the last tile's excess is zero-filled)
+  const int S = args.stages;
   const int nk = p.kpad / BK;
-  const int kb = (int)((int64_t)nk * r / ks), ke = (int)((int64_t)nk * (r + 1) / ks);
-  const int nloc = ke - kb;   // >= 1 (the launcher keeps ks <= nk)
-  const size_t a_bytes = (size_t)BM * BK * 2;
-  const size_t stage_bytes = a_bytes + (size_t)ntmax * BK * 2;
+  const int kb = (int)((int64_t)nk * r / KS), ke = (int)((int64_t)nk * (r + 1) / KS);
+  const int nloc = ke - kb;   // >= 1 (the launcher keeps KS <= nk)
+  const uint32_t a_bytes = BM * BK * 2;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)ntmax * BK * 2;
+  const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;   // swizzle atoms are 1024-byte aligned
+  unsigned char* const sbase = smem_raw + (base - saddr(smem_raw));
   const uint32_t tmem_cols = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
-  const __nv_bfloat16* YT = p.YT + (size_t)cbase * p.kpad;
+  constexpr int ROWS = BM / KS;   // rows of the tile updated by this CTA
+  constexpr int OCT = ROWS / 8;   // 8-row vectors per column
+  const int nvec = OCT * nt;
+  const int i_base = m0 + r * ROWS;
+
+  // y and V of this thread's first PF update vectors, loaded during the contraction
+  uint4 ypf[PF];
+  float4 vpf[PF][2];
+  auto load_vectors = [&](int g0) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int vi = g0 + tid + NTHREADS * u;
+      if (vi < nvec) {
+        const size_t off = (size_t)(cbase + vi / OCT) * p.kpad + i_base + 8 * (vi % OCT);
+        ypf[u] = __ldg(reinterpret_cast<const uint4*>(p.YT + off));
+        if (MOM) {
+          vpf[u][0] = *reinterpret_cast<const float4*>(p.VT + off);
+          vpf[u][1] = *reinterpret_cast<const float4*>(p.VT + off + 4);
+        }
+      }
+    }
+  };
+  load_vectors(0);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
@@ -168,99 +201,143 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(DenseStep p) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    for (int s = 0; s <= STAGES; ++s) mbar_init(&bars[s], 1);
+  if (tid == 32) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh_issued = 0;
+    sh_consumed = 0;
+    sh_timeout = 0;
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&args.tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&args.tmY)) : "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = idesc_bf16(BM, nt);
   bool timed_out = false;
 
-  // prologue: chunks 0 .. STAGES-2, one cp.async group each (empty past the end)
-  for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < nloc) {
-      unsigned char* sA = smem + (size_t)s * stage_bytes;
-      load_stage(sA, sA + a_bytes, p.A, p.kpad, YT, m0, (kb + s) * BK, nt, tid);
+  if (tid == 0) {
+    // TMA producer: chunk kc into stage kc % S once the MMAs of chunk kc - S have read it
+    int kc = 0;
+    for (; kc < nloc; ++kc) {
+      const int s = kc % S;
+      if (kc >= S && !mbar_wait(&empty[s], (uint32_t)(kc / S - 1) & 1u)) { timed_out = true; break; }
+      const uint32_t sa = base + (uint32_t)s * stage_bytes;
+      mbar_expect_tx(&full[s], stage_bytes);
+      tma_load_2d(sa, &args.tmA, (kb + kc) * BK, m0, &full[s]);
+      tma_load_2d(sa + a_bytes, &args.tmY, (kb + kc) * BK, cbase, &full[s]);
     }
-    cp_commit();
-  }
-  for (int kc = 0; kc < nloc; ++kc) {
-    const int s = kc % STAGES;
-    cp_wait<STAGES - 2>();   // this thread's copies of chunk kc have landed
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
-    __syncthreads();
-    if (tid == 0) {
+    sh_issued = kc;
+  } else if (tid == 32) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, nt);
+    int kc = 0;
+    for (; kc < nloc; ++kc) {
+      const int s = kc % S;
+      if (!mbar_wait(&full[s], (uint32_t)(kc / S) & 1u)) { timed_out = true; break; }
       tc_fence_after();
-      const uint32_t a0 = saddr(smem + (size_t)s * stage_bytes);
-      const uint32_t b0 = a0 + (uint32_t)a_bytes;
+      const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
-      for (int q = 0; q < BK / 16; ++q) {   // K = 16: two core matrices along K
-        const uint64_t ad = smem_desc(a0 + q * 256, 128, 1024);
-        const uint64_t bd = smem_desc(b0 + q * 256, 128, 1024);
-        mma_bf16(tmem, ad, bd, idesc, (kc > 0 || q > 0) ? 1u : 0u);
-      }
-      mma_commit(&bars[s]);   // stage s is free once these MMAs have read it
+      for (int q = 0; q < BK / 16; ++q)   // K = 16: 32 bytes along the swizzled 128-byte row
+        mma_bf16(tmem, desc_sw128(sa + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);   // stage s is free once these MMAs have read it
     }
-    // refill: chunk kc + STAGES - 1 into the stage of chunk kc - 1
-    const int kn = kc + STAGES - 1;
-    if (kn < nloc) {
-      const int sn = kn % STAGES;
-      if (kn >= STAGES && !mbar_wait(&bars[sn], (uint32_t)((kn - STAGES) / STAGES) & 1u)) timed_out = true;
-      unsigned char* sA = smem + (size_t)sn * stage_bytes;
-      load_stage(sA, sA + a_bytes, p.A, p.kpad, YT, m0, (kb + kn) * BK, nt, tid);
-    }
-    cp_commit();
+    sh_consumed = kc;
+    mma_commit(&done);         // arrives once every MMA issued above has completed
   }
-  cp_wait<0>();
-  if (tid == 0) mma_commit(&bars[STAGES]);   // tracks every MMA issued above
-  if (!mbar_wait(&bars[STAGES], 0)) timed_out = true;
+  __syncwarp();
+  if (!mbar_wait(&done, 0)) timed_out = true;
   tc_fence_after();
+  if (timed_out) atomicOr(&sh_timeout, 1);
+  cluster.sync();   // #1: every accumulator of the cluster is complete, every ring is free
+  if (tid == 0 && sh_timeout) {
+    // a wait gave up: let this CTA's issued loads land before its memory is reused
+    for (int kc = sh_consumed; kc < sh_issued; ++kc) (void)mbar_wait(&full[kc % S], (uint32_t)(kc / S) & 1u);
+  }
 
-  // partial product -> shared memory, column-major (part[c * 128 + row]):
-  // warp w reads tensor-memory lanes 32w .. 32w+31 (rows of the tile)
-  float* part = reinterpret_cast<float*>(smem);
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int c0 = 0; c0 < nt; c0 += 32) {
-    float g[32];
-    tmem_ld32(tl + (uint32_t)c0, g);
+  // push: row (TMEM lane) 32 warp + lane belongs to the CTA of rank row / ROWS;
+  // it receives the partial in recv[src][c][row % ROWS] (floats)
+  float* recv = reinterpret_cast<float*>(sbase);
+  {
+    const int row = warp * 32 + lane;
+    float* dst = cluster.map_shared_rank(recv, row / ROWS) + (size_t)r * nt * ROWS + (row % ROWS);
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < nt; c0 += 32) {
+      float g[32];
+      tmem_ld32(tl + (uint32_t)c0, g);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) part[(c0 + k) * BM + warp * 32 + lane] = g[k];
+      for (int k = 0; k < 32; ++k) dst[(size_t)(c0 + k) * ROWS] = g[k];
+    }
   }
   tc_fence_before();
-  cluster.sync();   // every partial of the tile is in place
+  cluster.sync();   // #2: every partial has arrived
   tc_fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 
-  // reduction over the ks partials and the fused update
-  const int rows_per = BM / ks;
-  const int lr = r * rows_per + tid % rows_per;   // row within the tile
-  const int i = m0 + lr;
+  // update: vector vi = (column c = vi / OCT, rows i_base + 8 (vi % OCT) .. + 7)
   bool bad = false;
-  if (i < p.n && !timed_out) {
-    const float dr = LAP ? p.dnet[i] : 0.0f;
-    for (int c = tid / rows_per; c < nt; c += ks) {
-      float acc = *cluster.map_shared_rank(part + c * BM + lr, 0);
-      for (int q = 1; q < ks; ++q) acc += *cluster.map_shared_rank(part + c * BM + lr, q);
+  for (int g0 = 0;;) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int vi = g0 + tid + NTHREADS * u;
+      if (vi >= nvec) continue;
+      const int c = vi / OCT, o = vi % OCT;
       const int col = cbase + c;
-      const size_t o = (size_t)col * p.kpad + i;
-      const float y = __bfloat162float(p.YT[o]);
-      const float grad = LAP ? fmaf(dr, y, -acc) : -acc;
-      float step = grad;
-      if (MOM) step = fmaf(p.mu, p.VT[o], grad);
+      const int i0 = i_base + 8 * o;
+      float acc[8];
+      {
+        const float4* src = reinterpret_cast<const float4*>(recv + (size_t)c * ROWS + 8 * o);
+        float4 a0 = src[0], a1 = src[1];
+        acc[0] = a0.x; acc[1] = a0.y; acc[2] = a0.z; acc[3] = a0.w;
+        acc[4] = a1.x; acc[5] = a1.y; acc[6] = a1.z; acc[7] = a1.w;
+#pragma unroll
+        for (int q = 1; q < KS; ++q) {   // partial sums added in rank order
+          const float4* sq = reinterpret_cast<const float4*>(recv + ((size_t)q * nt + c) * ROWS + 8 * o);
+          a0 = sq[0];
+          a1 = sq[1];
+          acc[0] += a0.x; acc[1] += a0.y; acc[2] += a0.z; acc[3] += a0.w;
+          acc[4] += a1.x; acc[5] += a1.y; acc[6] += a1.z; acc[7] += a1.w;
+        }
+      }
+      float y[8], v[8];
+      unpack8(ypf[u], y);
+      if (MOM) {
+        v[0] = vpf[u][0].x; v[1] = vpf[u][0].y; v[2] = vpf[u][0].z; v[3] = vpf[u][0].w;
+        v[4] = vpf[u][1].x; v[5] = vpf[u][1].y; v[6] = vpf[u][1].z; v[7] = vpf[u][1].w;
+      }
       const bool active = col < p.C && (!p.steps_cols || p.t < p.steps_cols[col]);
       const float alpha = p.alpha_cols ? p.afac * p.alpha_cols[col < p.C ? col : 0] : p.alpha;
-      float yn = fmaf(alpha, step, y);
-      if (active && !isfinite(yn)) bad = true;
-      yn = fminf(fmaxf(yn, -1.0f), 1.0f);
-      p.YTout[o] = __float2bfloat16_rn(active ? yn : y);
-      if (MOM && active) p.VT[o] = step;
+      float out[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        // rows >= n: y, V and the row of A are zero, so the new value is zero as well
+        const float dr = (LAP && i0 + k < p.n) ? __ldg(p.dnet + i0 + k) : 0.0f;
+        const float grad = LAP ? fmaf(dr, y[k], -acc[k]) : -acc[k];
+        const float step = MOM ? fmaf(p.mu, v[k], grad) : grad;
+        float yn = fmaf(alpha, step, y[k]);
+        if (active && !isfinite(yn)) bad = true;
+        yn = fminf(fmaxf(yn, -1.0f), 1.0f);
+        out[k] = active ? yn : y[k];
+        if (MOM) v[k] = step;
+      }
+      const size_t off = (size_t)col * p.kpad + i0;
+      *reinterpret_cast<uint4*>(p.YTout + off) =
+          make_uint4(pack_bf16x2(out[0], out[1]), pack_bf16x2(out[2], out[3]), pack_bf16x2(out[4], out[5]),
+                     pack_bf16x2(out[6], out[7]));
+      if (MOM && active) {
+        *reinterpret_cast<float4*>(p.VT + off) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(p.VT + off + 4) = make_float4(v[4], v[5], v[6], v[7]);
+      }
     }
+    g0 += NTHREADS * PF;
+    if (g0 >= nvec) break;
+    load_vectors(g0);
   }
-  cluster.sync();   // peers have finished reading this CTA's partial
   if (p.flag && (bad || timed_out)) atomicOr(p.flag, (bad ? 1 : 0) | (timed_out ? 2 : 0));
 }
 
@@ -311,11 +388,74 @@ int transpose(int32_t rows, int32_t cols, const T* in, int32_t ldin, T* out, int
   return DECO_OK;
 }
 
-std::atomic<int> g_smem_set[2][2];   // largest dynamic shared memory enabled per instance
+// largest dynamic shared memory enabled per kernel instance [MOM][LAP][log2 KS]
+std::atomic<int> g_smem_set[2][2][4];
+
+using KernelFn = void (*)(DenseArgs);
+
+template <bool MOM, bool LAP>
+KernelFn pick_ks(int ks) {
+  switch (ks) {
+    case 1: return k_dense_step<MOM, LAP, 1>;
+    case 2: return k_dense_step<MOM, LAP, 2>;
+    case 4: return k_dense_step<MOM, LAP, 4>;
+    default: return k_dense_step<MOM, LAP, 8>;
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+  });
+  return fn;
+}
+
+// BF16 matrix of `rows` x `cols` (row stride cols), boxes of 64 columns x box_rows rows, 128-byte swizzle
+int make_map(CUtensorMap* m, const void* base, int32_t cols, int32_t rows, int32_t box_rows) {
+  EncodeTiled enc = encode_tiled();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return DECO_ERR_CUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d BF16 matrix", (int)r, rows, cols);
+    return DECO_ERR_CUDA;
+  }
+  return DECO_OK;
+}
+
+int stages_for(int ntmax) {
+  const uint32_t stage = (uint32_t)BM * BK * 2 + (uint32_t)ntmax * BK * 2;
+  return std::max(2, std::min(MAX_STAGES, (int)(RING_BUDGET / stage)));
+}
 
 }  // namespace
 
-size_t dense_smem_bytes(int ntile) { return (size_t)STAGES * ((size_t)BM * BK * 2 + (size_t)ntile * BK * 2); }
+int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad,
+                    DenseMaps* maps) {
+  int rc = make_map(&maps->a, A, kpad, kpad, BM);
+  for (int i = 0; i < 2 && rc == DECO_OK; ++i) rc = make_map(&maps->y[i], yt[i], kpad, cpad, std::min(256, cpad));
+  return rc;
+}
 
 int dense_build(const deco_graph* g, int32_t kpad, __nv_bfloat16** out, cudaStream_t st) {
   const size_t bytes = (size_t)kpad * kpad * 2;
@@ -352,22 +492,31 @@ int dense_from_t(const void* yt, int32_t kpad, int32_t C, void* y, int32_t n, in
   return transpose<uint32_t>(C, n, static_cast<const uint32_t*>(yt), kpad, static_cast<uint32_t*>(y), ld, st);
 }
 
-int launch_dense_step(const DenseStep& p, cudaStream_t st) {
+int launch_dense_step(const DenseStep& p, const DenseMaps& maps, int which, cudaStream_t st) {
   const int nk = p.kpad / BK;
-  if (p.kpad % BM || p.cpad % 32 || p.cpad < 32 || p.ks < 1 || p.ks > 8 || (p.ks & (p.ks - 1)) || p.ks > nk) {
+  if (p.kpad % BM || p.cpad % 32 || p.cpad < 32 || p.ks < 1 || p.ks > 8 || (p.ks & (p.ks - 1)) || p.ks > nk ||
+      (which & ~1)) {
     set_error("dense step: bad shape (kpad=%d cpad=%d ks=%d)", p.kpad, p.cpad, p.ks);
     return DECO_ERR_ARG;
   }
-  const size_t smem = dense_smem_bytes(std::min(256, p.cpad));
+  const int ntmax = std::min(256, p.cpad);
+  const int S = stages_for(ntmax);
+  const size_t smem = (size_t)S * ((size_t)BM * BK * 2 + (size_t)ntmax * BK * 2) + 1024;   // + alignment slack
   const bool mom = p.mu != 0.0f, lap = p.objective == DECO_OBJ_LAPLACIAN;
-  void (*fn)(DenseStep) = mom ? (lap ? k_dense_step<true, true> : k_dense_step<true, false>)
-                              : (lap ? k_dense_step<false, true> : k_dense_step<false, false>);
-  std::atomic<int>& set = g_smem_set[mom][lap];
+  KernelFn fn = mom ? (lap ? pick_ks<true, true>(p.ks) : pick_ks<true, false>(p.ks))
+                    : (lap ? pick_ks<false, true>(p.ks) : pick_ks<false, false>(p.ks));
+  const int lk = p.ks == 1 ? 0 : (p.ks == 2 ? 1 : (p.ks == 4 ? 2 : 3));
+  std::atomic<int>& set = g_smem_set[mom][lap][lk];
   if (set.load() < (int)smem) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "dense step shared memory");
     set.store((int)smem);
   }
+  DenseArgs args;
+  args.tmA = maps.a;
+  args.tmY = maps.y[which];
+  args.p = p;
+  args.stages = S;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(p.kpad / BM * p.ks), (unsigned)((p.cpad + 255) / 256), 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
@@ -380,7 +529,7 @@ int launch_dense_step(const DenseStep& p, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, fn, p);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, fn, args);
   if (e != cudaSuccess) return cuda_fail(e, "dense step launch");
   return DECO_OK;
 }

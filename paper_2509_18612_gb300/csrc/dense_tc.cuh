@@ -1,12 +1,14 @@
 // Tensor-core step for dense graphs (DECO_KERNEL_DENSE): launch interface.
 #pragma once
 
+#include <cuda.h>
+
 #include "deco_internal.cuh"
 
 namespace deco {
 
 constexpr int DENSE_BM = 128;        // rows of A per CTA (tcgen05 M)
-constexpr int DENSE_BK = 64;         // contraction depth of one pipeline stage
+constexpr int DENSE_BK = 64;         // contraction depth of one pipeline stage (one 128-byte swizzle row)
 constexpr int DENSE_MAX_N = 32768;   // dense copy of A at most 2 GiB
 constexpr int DENSE_MAX_C = 1024;    // columns of the block (tiles of <= 256)
 constexpr int DENSE_MAX_W = 256;     // |w| exact in BF16
@@ -18,7 +20,6 @@ struct DenseStep {
   int32_t C;            // active columns
   int32_t ks;           // contraction split (cluster size along K)
   int objective;
-  const __nv_bfloat16* A;   // kpad x kpad, zero outside n x n
   const __nv_bfloat16* YT;  // cpad x kpad, transposed iterate (zero for nodes >= n)
   __nv_bfloat16* YTout;     // cpad x kpad, next iterate (distinct from YT)
   float* VT;                // cpad x kpad momentum (MOM only)
@@ -30,14 +31,22 @@ struct DenseStep {
   int32_t* flag;            // bit 0 nonfinite, bit 1 a bounded wait gave up
 };
 
+// TMA descriptors of the dense A and of the two transposed iterates
+struct DenseMaps {
+  CUtensorMap a;
+  CUtensorMap y[2];
+};
+
 // dense BF16 copy of A, row stride kpad, zero-filled (device memory owned by the graph)
 int dense_build(const deco_graph* g, int32_t kpad, __nv_bfloat16** out, cudaStream_t st);
+int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad,
+                    DenseMaps* maps);
 // y (n x ld, first C columns) -> yt (C x kpad), and back; esz 2 (BF16) or 4 (FP32)
 int dense_to_t(const void* y, int32_t n, int32_t ld, int32_t C, void* yt, int32_t kpad, size_t esz,
                cudaStream_t st);
 int dense_from_t(const void* yt, int32_t kpad, int32_t C, void* y, int32_t n, int32_t ld, size_t esz,
                  cudaStream_t st);
-int launch_dense_step(const DenseStep& p, cudaStream_t st);
-size_t dense_smem_bytes(int ntile);
+// one step: YT = yt[which] -> YTout = yt[which ^ 1] (p.YT / p.YTout must match)
+int launch_dense_step(const DenseStep& p, const DenseMaps& maps, int which, cudaStream_t st);
 
 }  // namespace deco

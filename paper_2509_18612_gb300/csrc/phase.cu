@@ -4,11 +4,11 @@
 // the global-memory kernel (step_global.cu) per step.
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "deco_internal.cuh"
 #include "phase.cuh"
-#include "dense_tc.cuh"
 #include "slab.cuh"
 
 namespace deco {
@@ -223,7 +223,9 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
     cudaError_t e = cudaMallocAsync((void**)&vt, elems * sizeof(float), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(transposed momentum)");
     if ((e = cudaMemsetAsync(vt, 0, elems * sizeof(float), st)) != cudaSuccess) return cuda_fail(e, "memset");
-    return DECO_OK;
+    maps = new (std::nothrow) DenseMaps;
+    if (!maps) { set_error("out of host memory"); return DECO_ERR_OOM; }
+    return dense_make_maps(g->dense, plan.kpad, yt, plan.cpad, maps);
   }
   if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
   {
@@ -301,7 +303,6 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     p.C = C;
     p.ks = plan.ks;
     p.objective = objective;
-    p.A = g->dense;
     p.VT = momv ? vt : nullptr;
     p.dnet = g->dnet;
     const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
@@ -316,7 +317,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
       p.YT = yt[c];
       p.YTout = yt[c ^ 1];
       p.t = t;
-      if ((rc = launch_dense_step(p, st))) return rc;
+      if ((rc = launch_dense_step(p, *maps, c, st))) return rc;
       c ^= 1;
     }
     if ((rc = dense_from_t(yt[c], kpad, C, y[cur], g->n, ld, 2, st))) return rc;
@@ -403,6 +404,8 @@ void PhaseRunner::release(cudaStream_t st) {
   }
   if (vt) cudaFreeAsync(vt, st);
   vt = nullptr;
+  delete maps;
+  maps = nullptr;
   xbuf = nullptr;
   vslab = nullptr;
   ypart = nullptr;

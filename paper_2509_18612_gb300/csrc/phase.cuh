@@ -3,6 +3,7 @@
 #pragma once
 
 #include "deco_internal.cuh"
+#include "dense_tc.cuh"
 #include "slab.cuh"
 
 namespace deco {
@@ -42,6 +43,7 @@ struct PhaseRunner {
   unsigned char* ypart = nullptr; // slab-major ping-pong partner of the column-slab schedule
   __nv_bfloat16* yt[2] = {nullptr, nullptr};   // dense kernel: transposed iterate pair
   float* vt = nullptr;                         // dense kernel: transposed momentum
+  DenseMaps* maps = nullptr;                   // dense kernel: TMA descriptors of A and yt[0], yt[1]
 
   // choose the kernel for a C-column block of g (builds the CSR image once)
   int prepare(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, cudaStream_t st);
