@@ -111,6 +111,10 @@ typedef enum deco_status {
  * DECO_KERNEL_DENSE it fixes the split of the contraction over k CTAs of a
  * cluster (k partial products reduced through distributed shared memory). */
 #define DECO_KERNEL_CLUSTER(k) ((k) << 8)
+/* With DECO_KERNEL_DENSE, one launch per step instead of the persistent phase
+ * kernel (one cooperative launch per phase, a grid barrier between steps, used
+ * when all its CTAs can be resident at once). */
+#define DECO_KERNEL_DENSE_PER_STEP (1 << 12)
 /* With DECO_KERNEL_ONCHIP, fixes the CTA size of the on-chip kernel. */
 #define DECO_KERNEL_THREADS_512 (1 << 12)
 #define DECO_KERNEL_THREADS_1024 (2 << 12)

@@ -341,6 +341,350 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
   if (p.flag && (bad || timed_out)) atomicOr(p.flag, (bad ? 1 : 0) | (timed_out ? 2 : 0));
 }
 
+// ---------------------------------------------------------------- persistent phase kernel
+//
+// All steps of a phase in one cooperative cluster launch (every CTA resident).
+// Warp 0 lane 0 loads (TMA), warp 1 lane 0 issues the MMAs, warps 2-5 run the
+// update; the stage ring runs on across steps.  Between steps a grid barrier
+// (a counter in global memory, bounded spin) orders the new YT of every CTA
+// before the next step's B tiles are loaded; the A tiles of the next step are
+// requested before that barrier, as A does not change.  The y and V of the
+// update vectors stay in registers for the whole phase (V is written back at
+// the end); the CTA's partial product is staged in shared memory as one block
+// per owning CTA and sent with one bulk shared-memory copy per peer, whose
+// bytes complete the owner's receive barrier.
+
+constexpr int PT = 192;          // threads of the phase kernel
+constexpr int PNV = 8;           // update vectors per thread at most
+constexpr int P_MAX_STAGES = 4;
+
+struct PhaseArgs {
+  CUtensorMap tmA;
+  CUtensorMap tmY[2];
+  DenseStep p;                   // YT / YTout unused: the phase ping-pongs yt[0] / yt[1]
+  __nv_bfloat16* yt[2];
+  unsigned int* gbar;            // grid barrier counter, zero at launch
+  int32_t steps;
+  int32_t w;                     // column tile width (multiple of 32, <= 128)
+  int32_t stages;
+  int32_t ncta;
+};
+
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_cluster(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 1; i < (1u << 30); ++i) {
+    if (mbar_try_cluster(bar, parity)) return true;
+    if ((i & 63u) == 0 && gtimer() - t0 > WAIT_NS) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// bulk copy of `bytes` from this CTA's shared memory into a peer's; the bytes
+// complete the peer's mbarrier (both given as shared::cluster addresses)
+__device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "r"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+// named barrier over `threads` threads that also ORs a predicate across them
+// (every update thread leaves a step on the same decision)
+__device__ __forceinline__ bool named_sync_or(int id, int threads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(threads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <bool MOM, bool LAP, int KS>
+__global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ PhaseArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[P_MAX_STAGES], empty[P_MAX_STAGES], done, recv_full;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int sh_timeout;
+  const DenseStep& p = args.p;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = (int)cluster.block_rank();
+  const int m0 = (int)(blockIdx.x / KS) * BM;
+  const int W = args.w;
+  const int cbase = (int)blockIdx.y * W;
+  const int nt = min(W, p.cpad - cbase);   // MMA N of this column tile, a multiple of 32
+  const int S = args.stages;
+  const int nk = p.kpad / BK;
+  const int kb = (int)((int64_t)nk * r / KS), ke = (int)((int64_t)nk * (r + 1) / KS);
+  const int nloc = ke - kb;
+  const uint32_t a_bytes = BM * BK * 2;
+  const uint32_t stage_bytes = a_bytes + (uint32_t)W * BK * 2;
+  const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
+  unsigned char* const sbase = smem_raw + (base - saddr(smem_raw));
+  constexpr int ROWS = BM / KS;
+  constexpr int OCT = ROWS / 8;
+  const uint32_t blk_bytes = (uint32_t)W * ROWS * 4;                       // one owner's share of the partial
+  float* const out = reinterpret_cast<float*>(sbase + (size_t)S * stage_bytes);   // [KS][W][ROWS]
+  float* const recv = out + (size_t)KS * W * ROWS;                                 // [KS-1][W][ROWS]
+  const uint32_t tmem_cols = nt <= 32 ? 32u : (nt <= 64 ? 64u : 128u);
+  const int nvec = OCT * nt;
+  const int i_base = m0 + r * ROWS;
+
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_init(&recv_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh_timeout = 0;
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&args.tmA)) : "memory");
+  }
+  tc_fence_before();
+  cluster.sync();   // barriers initialised and every CTA of the cluster running
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool timed_out = false;
+
+  if (tid == 0) {
+    // ---------------- TMA producer
+    int64_t g = 0;   // chunk counter over the whole phase
+    for (int t = 0; t < args.steps && !timed_out; ++t) {
+      const CUtensorMap* tmY = &args.tmY[t & 1];
+      const int pre = min(S, nloc);
+      // A tiles of the first stages of this step: no dependence on the new iterate
+      for (int kc = 0; kc < pre; ++kc) {
+        const int64_t gg = g + kc;
+        const int s = (int)(gg % S);
+        if (gg >= S && !mbar_wait(&empty[s], (uint32_t)(gg / S - 1) & 1u)) { timed_out = true; break; }
+        mbar_expect_tx(&full[s], stage_bytes);
+        tma_load_2d(base + (uint32_t)s * stage_bytes, &args.tmA, (kb + kc) * BK, m0, &full[s]);
+      }
+      if (timed_out) break;
+      if (t > 0) {
+        // grid barrier: every CTA has written its rows of the iterate of step t
+        const uint32_t target = (uint32_t)args.ncta * (uint32_t)t;
+        bool ok = ld_acquire(args.gbar) >= target;
+        const uint64_t t0 = gtimer();
+        for (uint32_t i = 0; !ok && i < (1u << 30); ++i) {
+          ok = ld_acquire(args.gbar) >= target;
+          if ((i & 63u) == 0 && gtimer() - t0 > WAIT_NS) break;
+        }
+        if (!ok) { timed_out = true; break; }
+        asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
+      }
+      for (int kc = 0; kc < pre; ++kc) {
+        const int s = (int)((g + kc) % S);
+        tma_load_2d(base + (uint32_t)s * stage_bytes + a_bytes, tmY, (kb + kc) * BK, cbase, &full[s]);
+      }
+      for (int kc = pre; kc < nloc; ++kc) {
+        const int64_t gg = g + kc;
+        const int s = (int)(gg % S);
+        if (!mbar_wait(&empty[s], (uint32_t)(gg / S - 1) & 1u)) { timed_out = true; break; }
+        const uint32_t sa = base + (uint32_t)s * stage_bytes;
+        mbar_expect_tx(&full[s], stage_bytes);
+        tma_load_2d(sa, &args.tmA, (kb + kc) * BK, m0, &full[s]);
+        tma_load_2d(sa + a_bytes, tmY, (kb + kc) * BK, cbase, &full[s]);
+      }
+      g += nloc;
+    }
+  } else if (tid == 32) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, nt);
+    int64_t g = 0;
+    for (int t = 0; t < args.steps && !timed_out; ++t) {
+      for (int kc = 0; kc < nloc; ++kc, ++g) {
+        const int s = (int)(g % S);
+        if (!mbar_wait(&full[s], (uint32_t)(g / S) & 1u)) { timed_out = true; break; }
+        tc_fence_after();
+        const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+#pragma unroll
+        for (int q = 0; q < BK / 16; ++q)
+          mma_bf16(tmem, desc_sw128(sa + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&done);   // phase t of `done`: the accumulator of step t is complete
+    }
+  } else if (warp >= 2) {
+    // ---------------- update warps: et = row-vector owner index, quarter = TMEM lanes
+    const int et = tid - 64;
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;   // tile row read from tensor memory
+    const int qown = row / ROWS;
+    uint4 yr[PNV];
+    float vr[PNV][8];
+    float acol[PNV];
+    int32_t scol[PNV];
+#pragma unroll
+    for (int u = 0; u < PNV; ++u) {
+      const int vi = et + 128 * u;
+      yr[u] = make_uint4(0, 0, 0, 0);
+      acol[u] = 0.0f;
+      scol[u] = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) vr[u][k] = 0.0f;
+      if (vi < nvec) {
+        const int col = cbase + vi / OCT;
+        const size_t off = (size_t)col * p.kpad + i_base + 8 * (vi % OCT);
+        yr[u] = *reinterpret_cast<const uint4*>(args.yt[0] + off);
+        if (MOM) {
+          const float4 a = *reinterpret_cast<const float4*>(p.VT + off);
+          const float4 b = *reinterpret_cast<const float4*>(p.VT + off + 4);
+          vr[u][0] = a.x; vr[u][1] = a.y; vr[u][2] = a.z; vr[u][3] = a.w;
+          vr[u][4] = b.x; vr[u][5] = b.y; vr[u][6] = b.z; vr[u][7] = b.w;
+        }
+        acol[u] = p.alpha_cols ? p.afac * p.alpha_cols[col < p.C ? col : 0] : p.alpha;
+        scol[u] = col < p.C ? (p.steps_cols ? p.steps_cols[col] : INT32_MAX) : -1;   // -1: padding column
+      }
+    }
+    bool bad = false;
+    for (int t = 0; t < args.steps && !timed_out; ++t) {
+      if (KS > 1 && et == 0) mbar_expect_tx(&recv_full, (uint32_t)(KS - 1) * blk_bytes);
+      if (named_sync_or(1, 128, !mbar_wait(&done, (uint32_t)t & 1u))) { timed_out = true; break; }
+      tc_fence_after();
+      // accumulator -> out[owner][c][row % ROWS]
+      {
+        float* dst = out + (size_t)qown * W * ROWS + (row % ROWS);
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        for (int c0 = 0; c0 < nt; c0 += 32) {
+          float gv[32];
+          tmem_ld32(tl + (uint32_t)c0, gv);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) dst[(size_t)(c0 + k) * ROWS] = gv[k];
+        }
+      }
+      tc_fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged rows -> bulk copy reads
+      named_sync(1, 128);
+      if (KS > 1 && et == 0) {
+        for (int q = 0; q < KS; ++q) {
+          if (q == r) continue;
+          const int slot = r < q ? r : r - 1;   // this CTA's slot in q's receive area
+          bulk_to_peer(mapa(saddr(recv + (size_t)slot * W * ROWS), (uint32_t)q),
+                       saddr(out + (size_t)q * W * ROWS), blk_bytes, mapa(saddr(&recv_full), (uint32_t)q));
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+      if (KS > 1 && named_sync_or(1, 128, !mbar_wait_cluster(&recv_full, (uint32_t)t & 1u))) {
+        timed_out = true;
+        break;
+      }
+      __nv_bfloat16* YTo = args.yt[(t + 1) & 1];
+#pragma unroll
+      for (int u = 0; u < PNV; ++u) {
+        const int vi = et + 128 * u;
+        if (vi >= nvec) continue;
+        const int c = vi / OCT, o = vi % OCT;
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KS; ++q) {   // partial sums added in rank order
+          const float* src = q == r ? out + ((size_t)r * W + c) * ROWS + 8 * o
+                                    : recv + ((size_t)(q < r ? q : q - 1) * W + c) * ROWS + 8 * o;
+          const float4 a0 = reinterpret_cast<const float4*>(src)[0];
+          const float4 a1 = reinterpret_cast<const float4*>(src)[1];
+          if (q == 0) {
+            acc[0] = a0.x; acc[1] = a0.y; acc[2] = a0.z; acc[3] = a0.w;
+            acc[4] = a1.x; acc[5] = a1.y; acc[6] = a1.z; acc[7] = a1.w;
+          } else {
+            acc[0] += a0.x; acc[1] += a0.y; acc[2] += a0.z; acc[3] += a0.w;
+            acc[4] += a1.x; acc[5] += a1.y; acc[6] += a1.z; acc[7] += a1.w;
+          }
+        }
+        const int i0 = i_base + 8 * o;
+        float y[8];
+        unpack8(yr[u], y);
+        const bool active = t < scol[u];
+        float outv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          // rows >= n: y, V and the row of A are zero, so the new value is zero as well
+          const float dr = (LAP && i0 + k < p.n) ? __ldg(p.dnet + i0 + k) : 0.0f;
+          const float grad = LAP ? fmaf(dr, y[k], -acc[k]) : -acc[k];
+          const float step = MOM ? fmaf(p.mu, vr[u][k], grad) : grad;
+          float yn = fmaf(acol[u], step, y[k]);
+          if (active && !isfinite(yn)) bad = true;
+          yn = fminf(fmaxf(yn, -1.0f), 1.0f);
+          outv[k] = active ? yn : y[k];
+          if (MOM && active) vr[u][k] = step;
+        }
+        yr[u] = make_uint4(pack_bf16x2(outv[0], outv[1]), pack_bf16x2(outv[2], outv[3]),
+                           pack_bf16x2(outv[4], outv[5]), pack_bf16x2(outv[6], outv[7]));
+        *reinterpret_cast<uint4*>(YTo + (size_t)(cbase + c) * p.kpad + i0) = yr[u];
+      }
+      if (KS > 1 && et == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // `out` reusable
+      asm volatile("fence.proxy.async.global;" ::: "memory");   // new rows -> the next step's TMA reads
+      named_sync(1, 128);
+      if (et == 0 && t + 1 < args.steps) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(args.gbar) : "memory");
+      }
+    }
+    if (MOM) {
+#pragma unroll
+      for (int u = 0; u < PNV; ++u) {
+        const int vi = et + 128 * u;
+        if (vi >= nvec || scol[u] < 0) continue;
+        const size_t off = (size_t)(cbase + vi / OCT) * p.kpad + i_base + 8 * (vi % OCT);
+        *reinterpret_cast<float4*>(p.VT + off) = make_float4(vr[u][0], vr[u][1], vr[u][2], vr[u][3]);
+        *reinterpret_cast<float4*>(p.VT + off + 4) = make_float4(vr[u][4], vr[u][5], vr[u][6], vr[u][7]);
+      }
+    }
+    if (p.flag && bad) atomicOr(p.flag, 1);
+  }
+  __syncwarp();
+  if (timed_out) atomicOr(&sh_timeout, 1);
+  __syncthreads();
+  if (sh_timeout) {
+    // a wait gave up: report it, and give this CTA's own loads and copies
+    // still in flight time to land (100 us, far above their latency)
+    if (tid == 0) {
+      if (p.flag) atomicOr(p.flag, 2);
+      const uint64_t t0 = gtimer();
+      while (gtimer() - t0 < 100000ull) {
+      }
+    }
+    if (tid == 64) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncthreads();
+  }
+  tc_fence_before();
+  cluster.sync();   // no peer copies into this CTA any more
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
 // ---- dense copy of A: one warp per row
 __global__ void k_dense_from_csr(int32_t n, int32_t kpad, int wmode, const int32_t* row_ptr,
                                  const int32_t* col_idx, const uint32_t* col_sw, const float* w,
@@ -450,11 +794,37 @@ int stages_for(int ntmax) {
 
 }  // namespace
 
-int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad,
+int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad, int w,
                     DenseMaps* maps) {
   int rc = make_map(&maps->a, A, kpad, kpad, BM);
   for (int i = 0; i < 2 && rc == DECO_OK; ++i) rc = make_map(&maps->y[i], yt[i], kpad, cpad, std::min(256, cpad));
+  for (int i = 0; i < 2 && rc == DECO_OK && w > 0; ++i) rc = make_map(&maps->yw[i], yt[i], kpad, cpad, w);
   return rc;
+}
+
+int dense_phase_shape(int32_t kpad, int32_t cpad, int ks, int w, DensePhaseShape* out) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    optin = 227 * 1024;
+  }
+  const int rows = BM / ks;
+  const size_t out_b = (size_t)ks * w * rows * 4, recv_b = (size_t)(ks - 1) * w * rows * 4;
+  const size_t stage = (size_t)BM * BK * 2 + (size_t)w * BK * 2;
+  const long long room = (long long)optin - 1024 - 512 - (long long)(out_b + recv_b);
+  const int S = room > 0 ? (int)std::min<long long>(P_MAX_STAGES, room / (long long)stage) : 0;
+  const int nk = kpad / BK;
+  if (S < 2 || w < 32 || w > 128 || w % 32 || ks > nk || (ks & (ks - 1)) || ks > 8 || (w + 8 * ks - 1) / (8 * ks) > PNV) {
+    set_error("dense phase kernel: no shape for w=%d ks=%d", w, ks);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  out->w = w;
+  out->ks = ks;
+  out->stages = S;
+  out->smem = (size_t)S * stage + out_b + recv_b + 1024;
+  out->ctas = kpad / BM * ks * ((cpad + w - 1) / w);
+  return DECO_OK;
 }
 
 int dense_build(const deco_graph* g, int32_t kpad, __nv_bfloat16** out, cudaStream_t st) {
@@ -490,6 +860,85 @@ int dense_from_t(const void* yt, int32_t kpad, int32_t C, void* y, int32_t n, in
   if (esz == 2)
     return transpose<uint16_t>(C, n, static_cast<const uint16_t*>(yt), kpad, static_cast<uint16_t*>(y), ld, st);
   return transpose<uint32_t>(C, n, static_cast<const uint32_t*>(yt), kpad, static_cast<uint32_t*>(y), ld, st);
+}
+
+namespace {
+
+using PhaseFn = void (*)(PhaseArgs);
+
+template <bool MOM, bool LAP>
+PhaseFn pick_phase(int ks) {
+  switch (ks) {
+    case 1: return k_dense_phase<MOM, LAP, 1>;
+    case 2: return k_dense_phase<MOM, LAP, 2>;
+    case 4: return k_dense_phase<MOM, LAP, 4>;
+    default: return k_dense_phase<MOM, LAP, 8>;
+  }
+}
+
+std::atomic<int> g_phase_smem[2][2][4];
+
+}  // namespace
+
+int launch_dense_phase(const DenseStep& p, const DenseMaps& maps, __nv_bfloat16* const yt[2],
+                       const DensePhaseShape& sh, int32_t steps, unsigned int* gbar, cudaStream_t st) {
+  if (steps <= 0) return DECO_OK;
+  const bool mom = p.mu != 0.0f, lap = p.objective == DECO_OBJ_LAPLACIAN;
+  PhaseFn fn = mom ? (lap ? pick_phase<true, true>(sh.ks) : pick_phase<true, false>(sh.ks))
+                   : (lap ? pick_phase<false, true>(sh.ks) : pick_phase<false, false>(sh.ks));
+  const int lk = sh.ks == 1 ? 0 : (sh.ks == 2 ? 1 : (sh.ks == 4 ? 2 : 3));
+  std::atomic<int>& set = g_phase_smem[mom][lap][lk];
+  if (set.load() < (int)sh.smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "dense phase shared memory");
+    set.store((int)sh.smem);
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(p.kpad / BM * sh.ks), (unsigned)((p.cpad + sh.w - 1) / sh.w), 1);
+  cfg.blockDim = dim3(PT, 1, 1);
+  cfg.dynamicSmemBytes = sh.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)sh.ks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // every CTA waits on every other between steps: all of them must be resident at once
+  int clusters = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+  if (e != cudaSuccess || (int64_t)clusters * sh.ks < sh.ctas) {
+    cudaGetLastError();
+    set_error("dense phase kernel: %d CTAs cannot all be resident (%d clusters of %d)", sh.ctas, clusters, sh.ks);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  PhaseArgs args;
+  args.tmA = maps.a;
+  args.tmY[0] = maps.yw[0];
+  args.tmY[1] = maps.yw[1];
+  args.p = p;
+  args.yt[0] = yt[0];
+  args.yt[1] = yt[1];
+  args.gbar = gbar;
+  args.steps = steps;
+  args.w = sh.w;
+  args.stages = sh.stages;
+  args.ncta = sh.ctas;
+  if ((e = cudaMemsetAsync(gbar, 0, sizeof(unsigned int), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.numAttrs = 2;
+  e = cudaLaunchKernelEx(&cfg, fn, args);
+  if (e != cudaSuccess) {
+    // a driver that does not combine cooperative and cluster launches: the
+    // occupancy check above already guarantees residency
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, fn, args);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dense phase launch");
+  return DECO_OK;
 }
 
 int launch_dense_step(const DenseStep& p, const DenseMaps& maps, int which, cudaStream_t st) {

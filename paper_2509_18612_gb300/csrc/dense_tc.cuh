@@ -31,16 +31,34 @@ struct DenseStep {
   int32_t* flag;            // bit 0 nonfinite, bit 1 a bounded wait gave up
 };
 
-// TMA descriptors of the dense A and of the two transposed iterates
+// TMA descriptors of the dense A and of the two transposed iterates, with the
+// B boxes of the per-step kernel (min(256, cpad) rows) and of the phase kernel (w rows)
 struct DenseMaps {
   CUtensorMap a;
   CUtensorMap y[2];
+  CUtensorMap yw[2];
+};
+
+// launch shape of the persistent phase kernel
+struct DensePhaseShape {
+  int w = 0;          // column tile width (multiple of 32, <= 128)
+  int ks = 1;         // contraction split (cluster size)
+  int stages = 0;     // TMA stage ring depth
+  size_t smem = 0;    // dynamic shared memory
+  int ctas = 0;       // row tiles x ks x column tiles
 };
 
 // dense BF16 copy of A, row stride kpad, zero-filled (device memory owned by the graph)
 int dense_build(const deco_graph* g, int32_t kpad, __nv_bfloat16** out, cudaStream_t st);
-int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad,
+int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad, int w,
                     DenseMaps* maps);
+// shape of the phase kernel for split ks and width w; DECO_ERR_UNSUPPORTED if it
+// does not fit in shared memory
+int dense_phase_shape(int32_t kpad, int32_t cpad, int ks, int w, DensePhaseShape* out);
+// all `steps` steps in one launch; the result is in yt[steps & 1].
+// DECO_ERR_UNSUPPORTED (nothing launched) if its CTAs cannot all be resident.
+int launch_dense_phase(const DenseStep& p, const DenseMaps& maps, __nv_bfloat16* const yt[2],
+                       const DensePhaseShape& sh, int32_t steps, unsigned int* gbar, cudaStream_t st);
 // y (n x ld, first C columns) -> yt (C x kpad), and back; esz 2 (BF16) or 4 (FP32)
 int dense_to_t(const void* y, int32_t n, int32_t ld, int32_t C, void* yt, int32_t kpad, size_t esz,
                cudaStream_t st);

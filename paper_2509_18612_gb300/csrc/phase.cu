@@ -66,7 +66,8 @@ bool valid_selector(int kernel) {
   const int s = (kernel >> 16) & 0xF;
   if (kernel & ~0xFFFFF) return false;
   if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_DENSE || t == 3 || x == 3) return false;
-  if ((t || x) && kind != DECO_KERNEL_ONCHIP) return false;
+  if (x && kind != DECO_KERNEL_ONCHIP) return false;
+  if (t && kind != DECO_KERNEL_ONCHIP && !(kind == DECO_KERNEL_DENSE && t == 1)) return false;
   if (k && kind != DECO_KERNEL_ONCHIP && kind != DECO_KERNEL_DENSE) return false;
   if (s && (kind != DECO_KERNEL_GLOBAL || s > 6)) return false;
   if (k && ((k & (k - 1)) || k > 8)) return false;
@@ -93,7 +94,7 @@ void record_tuning(const deco_graph* g, int32_t C, int prec, int kernel) {
 // Dense tensor-core kernel: limits, padding and the contraction split (the
 // largest power of two <= 8 that keeps row tiles x column tiles x split within
 // one wave of the SMs, unless fixed by the caller).
-static int plan_dense(const deco_graph* g, int32_t C, int want_k, PhasePlan* plan) {
+static int plan_dense(const deco_graph* g, int32_t C, int want_k, bool per_step, PhasePlan* plan) {
   if (g->n < 1 || g->n > DENSE_MAX_N || C > DENSE_MAX_C || g->max_abs_w > DENSE_MAX_W) {
     set_error("the dense kernel needs n <= %d, C <= %d and |w| <= %d (n=%d, C=%d, max |w|=%d)", DENSE_MAX_N,
               DENSE_MAX_C, DENSE_MAX_W, g->n, C, g->max_abs_w);
@@ -114,6 +115,23 @@ static int plan_dense(const deco_graph* g, int32_t C, int want_k, PhasePlan* pla
     return DECO_ERR_UNSUPPORTED;
   }
   plan->ks = ks;
+  if (!per_step) {
+    // persistent phase kernel: column tiles of <= 128, the largest split whose
+    // CTAs fit in one wave (residency is checked again at launch)
+    const int w = std::min(128, plan->cpad);
+    const int64_t tiles_p = (int64_t)(plan->kpad / DENSE_BM) * ((plan->cpad + w - 1) / w);
+    for (int kp = 8; kp >= 1; kp /= 2) {
+      if (want_k && kp != want_k) continue;
+      if (!want_k && tiles_p * kp > device_sm_count()) continue;
+      DensePhaseShape sh;
+      if (dense_phase_shape(plan->kpad, plan->cpad, kp, w, &sh) == DECO_OK) {
+        plan->dpersist = true;
+        plan->dphase = sh;
+        break;
+      }
+      clear_error();
+    }
+  }
   return DECO_OK;
 }
 
@@ -137,7 +155,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   if (force == DECO_KERNEL_DENSE) {
     // BF16 blocks only; an FP32 block (e.g. the FP32 polish) is planned as AUTO
     if (prec != DECO_PREC_BF16) return plan_phase(g, C, ld, prec, DECO_KERNEL_AUTO, plan);
-    return plan_dense(g, C, want_k, plan);
+    return plan_dense(g, C, want_k, want_t == 1, plan);
   }
   plan->threads = want_t == 1 ? 512 : 1024;
   plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
@@ -225,7 +243,11 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
     if ((e = cudaMemsetAsync(vt, 0, elems * sizeof(float), st)) != cudaSuccess) return cuda_fail(e, "memset");
     maps = new (std::nothrow) DenseMaps;
     if (!maps) { set_error("out of host memory"); return DECO_ERR_OOM; }
-    return dense_make_maps(g->dense, plan.kpad, yt, plan.cpad, maps);
+    if (plan.dpersist) {
+      if ((e = cudaMallocAsync((void**)&gbar, sizeof(unsigned int), st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync(grid barrier)");
+    }
+    return dense_make_maps(g->dense, plan.kpad, yt, plan.cpad, plan.dpersist ? plan.dphase.w : 0, maps);
   }
   if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
   {
@@ -313,7 +335,19 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     p.steps_cols = steps_cols;
     p.flag = flag;
     int c = 0;
-    for (int32_t t = 0; t < steps; ++t) {
+    bool done = false;
+    if (plan.dpersist) {
+      rc = launch_dense_phase(p, *maps, yt, plan.dphase, steps, gbar, st);
+      if (rc == DECO_OK) {
+        done = true;
+        c = steps & 1;
+      } else if (rc == DECO_ERR_UNSUPPORTED) {
+        clear_error();   // not every CTA can be resident now: one launch per step instead
+      } else {
+        return rc;
+      }
+    }
+    for (int32_t t = 0; t < steps && !done; ++t) {
       p.YT = yt[c];
       p.YTout = yt[c ^ 1];
       p.t = t;
@@ -322,7 +356,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     }
     if ((rc = dense_from_t(yt[c], kpad, C, y[cur], g->n, ld, 2, st))) return rc;
     if (momv && store_v && (rc = dense_from_t(vt, kpad, C, v, g->n, ld, 4, st))) return rc;
-    if (kernels) *kernels += steps + 2 + (momv ? 1 + (store_v ? 1 : 0) : 0);
+    if (kernels) *kernels += (done ? 1 : steps) + 2 + (momv ? 1 + (store_v ? 1 : 0) : 0);
     return DECO_OK;
   }
   StepLaunch sl{};
@@ -406,6 +440,8 @@ void PhaseRunner::release(cudaStream_t st) {
   vt = nullptr;
   delete maps;
   maps = nullptr;
+  if (gbar) cudaFreeAsync(gbar, st);
+  gbar = nullptr;
   xbuf = nullptr;
   vslab = nullptr;
   ypart = nullptr;

@@ -20,8 +20,10 @@ struct PhasePlan {
   int items = 0;                 // column slabs
   int32_t max_own = 0, max_img_words = 0;
   SlabImage image;               // on-chip CSR image (owned by the graph)
-  int ks = 1;                    // dense kernel: contraction split over a cluster
+  int ks = 1;                    // dense kernel: contraction split over a cluster (per-step launches)
   int32_t kpad = 0, cpad = 0;    // dense kernel: padded n and C
+  bool dpersist = false;         // dense kernel: one persistent launch per phase
+  DensePhaseShape dphase;        // its shape
 };
 
 int device_sm_count();
@@ -44,6 +46,7 @@ struct PhaseRunner {
   __nv_bfloat16* yt[2] = {nullptr, nullptr};   // dense kernel: transposed iterate pair
   float* vt = nullptr;                         // dense kernel: transposed momentum
   DenseMaps* maps = nullptr;                   // dense kernel: TMA descriptors of A and yt[0], yt[1]
+  unsigned int* gbar = nullptr;                // dense phase kernel: grid barrier counter
 
   // choose the kernel for a C-column block of g (builds the CSR image once)
   int prepare(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, cudaStream_t st);

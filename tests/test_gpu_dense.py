@@ -87,17 +87,44 @@ def test_dense_step_bitwise_equals_global_on_dyadic_block(name, C, objective, mu
     alpha = 0.01 if objective == O.OBJ_MULTILINEAR01 else 0.003
     ref = run_phase(g, Y, V, C, ld, 1, objective, alpha, mu, deco.DECO_KERNEL_GLOBAL)
     G = deco.graph_from(g)
-    for k in (0, 1, 2, 4, 8):
+    for k, mode in [(k, m) for k in (0, 1, 2, 4, 8) for m in (0, deco.DECO_KERNEL_DENSE_PER_STEP)]:
         try:
-            got = run_phase(g, Y, V, C, ld, 1, objective, alpha, mu, DENSE | (k << 8), G=G)
+            got = run_phase(g, Y, V, C, ld, 1, objective, alpha, mu, DENSE | (k << 8) | mode, G=G)
         except deco.DecoError as e:   # a split deeper than the contraction of a small graph
             assert e.status == deco.DECO_ERR_UNSUPPORTED and k > 1
             continue
         assert got[2] == ref[2] == 0
-        assert torch.equal(got[0][:, :C], ref[0][:, :C]), k
+        assert torch.equal(got[0][:, :C], ref[0][:, :C]), (k, mode)
         if mu:
-            assert torch.equal(got[1][:, :C], ref[1][:, :C]), k
+            assert torch.equal(got[1][:, :C], ref[1][:, :C]), (k, mode)
         assert torch.equal(got[0][:, C:], to_dev(Y).to(torch.bfloat16)[:, C:])   # padding columns untouched
+
+
+@pytest.mark.parametrize("name", ["er1000_dense", "signed_dense", "er100"])
+@pytest.mark.parametrize("k", [0, 1, 2, 4, 8])
+def test_dense_phase_kernel_bitwise_equals_per_step_launches(name, k):
+    # the persistent phase kernel and one launch per step split the
+    # contraction the same way and add the partials in the same order
+    g = GRAPHS[name]()
+    C, ld = 136, 192
+    rng = np.random.default_rng(10)
+    Y = np.zeros((g.n, ld), np.float32)
+    Y[:, :C] = rng.uniform(-1, 1, size=(g.n, C)) * np.where(rng.random(C) < 0.5, 1.0, 1e-3)
+    V = np.zeros((g.n, ld), np.float32)
+    V[:, :C] = rng.normal(size=(g.n, C)) * 0.1
+    sc = to_dev(rng.integers(0, 30, C).astype(np.int32))
+    ac = to_dev(rng.uniform(1e-5, 1e-3, C).astype(np.float32))
+    objective = O.OBJ_LAPLACIAN if name == "signed_dense" else O.OBJ_MULTILINEAR01
+    G = deco.graph_from(g)
+    out = []
+    for mode in (0, deco.DECO_KERNEL_DENSE_PER_STEP):
+        try:
+            out.append(run_phase(g, Y, V, C, ld, 24, objective, 0.0, 0.9, DENSE | (k << 8) | mode, ac, sc, G=G))
+        except deco.DecoError as e:
+            assert e.status == deco.DECO_ERR_UNSUPPORTED and k > 1
+            pytest.skip("split deeper than the contraction")
+    assert out[0][2] == out[1][2] == 0
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
 
 
 def test_dense_per_column_alpha_and_budget_bitwise():
