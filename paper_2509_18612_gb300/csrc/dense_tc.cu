@@ -646,10 +646,8 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       if (KS > 1 && et == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // `out` reusable
       asm volatile("fence.proxy.async.global;" ::: "memory");   // new rows -> the next step's TMA reads
       named_sync(1, 128);
-      if (et == 0 && t + 1 < args.steps) {
-        __threadfence();
+      if (et == 0 && t + 1 < args.steps)
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(args.gbar) : "memory");
-      }
     }
     if (MOM) {
 #pragma unroll
