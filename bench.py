@@ -71,33 +71,42 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 50):
         self.index = index
+        self.period_ms = period_ms
         self.samples = []
-        self._stop = threading.Event()
+        self._proc = None
         self._t = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._proc.stdout:
+            line = line.strip()
+            if line:
+                self.samples.append([x.strip() for x in line.split(",")])
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        # one nvidia-smi process in loop mode for the whole timed region
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                           "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.1)   # first sample before the timed work starts
+        except Exception:
+            self._proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
+        if self._proc is not None:
+            time.sleep(self.period_ms / 1000.0)
+            self._proc.terminate()   # the child started above, by its own handle
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._t:
-            self._t.join(timeout=10)
+            self._t.join(timeout=5)
 
     def summary(self):
         if not self.samples:
@@ -413,7 +422,7 @@ def run_er4096_dense():
                             "cut_gap_bf16_dense_vs_fp32": (res_f.best_cut - res_d.best_cut) / res_f.best_cut},
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_kind": kind + " (burst)",
-                         "kernel": "k_dense_step (one step)", "us_per_launch": t_step * 1e6,
+                         "kernel": "k_dense_phase (per step of a phase launch)", "us_per_step": t_step * 1e6,
                          "algorithmic_flops_per_launch": flops}}
 
 
