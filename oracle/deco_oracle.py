@@ -56,6 +56,7 @@ STREAM_INIT = 0      # per-(row, column) draws of the starting block
 STREAM_IDI = 1       # per-node coins of the IDI mean
 STREAM_DUI = 2       # per-node uniform draw of the DUI mean
 STREAM_EVOLVE = 3    # perturbations of the evolution-based search
+STREAM_ORDER = 6     # random vertex orderings of the greedy comparator
 
 
 # ----------------------------------------------------------------------------
@@ -407,6 +408,7 @@ class Params:
     beta: float = 0.2
     uniform_half_width: float = 1.0
     mean: Optional[np.ndarray] = None   # for init == "mean" (e.g. a learned proposal)
+    local_search: int = 0     # rounds of 1-flip local search on every phase's rounded vectors (0: off)
 
 
 @dataclass
@@ -484,6 +486,8 @@ def solve(g, B: int, phases: Sequence[Phase], params: Params, seed: int, x0=None
             Y = gaussian_block(h, B * ph.lift, seed, k, params.eta, params.scale)
         Y = run_phase(g, Y, ph, params.objective)
         Z = binarize(Y, ph.lift)
+        if params.local_search > 0:
+            Z, _ = local_search(g, Z, params.local_search)
         cuts = cut_values(g, Z)
         b = best_of(cuts)
         phase_cuts.append(cuts)
@@ -673,3 +677,83 @@ def greedy_maxcut(g, order) -> np.ndarray:
         gain0 = float(np.sum(wt[placed & (side[nb] == 1)]))   # put v in S-bar
         side[v] = 1 if gain1 >= gain0 else 0
     return side.astype(np.uint8)
+
+
+def feistel_order(n: int, b: int, seed: int) -> np.ndarray:
+    """A random ordering of the n vertices for greedy run b (App. C.1 draws a
+    fresh random ordering for every run).
+
+    The ordering is the bijection k -> pi_b(k) of [0, n): a 4-round balanced
+    Feistel network on [0, 4^h) (h >= 1 bits per half, 4^h >= n) whose round i
+    maps (L, R) to (R, L xor (F_i(R) mod 2^h)), F_i(R) = word 0 of Philox
+    counter (R, b, i, STREAM_ORDER), key seed; values >= n are walked through
+    the network again until they fall in [0, n) (cycle walking keeps the map a
+    bijection).  Returns order[k] = pi_b(k).
+    """
+    h = 1
+    while 4 ** h < n:
+        h += 1
+    mask = np.uint64((1 << h) - 1)
+    k0, k1 = seed_key(seed)
+
+    def net(x):
+        L, R = x >> np.uint64(h), x & mask
+        for i in range(4):
+            f, _, _, _ = philox4x32_10(R, np.uint64(b), np.uint64(i), np.uint64(STREAM_ORDER), k0, k1)
+            L, R = R, L ^ (f.astype(np.uint64) & mask)
+        return (L << np.uint64(h)) | R
+
+    x = np.arange(n, dtype=np.uint64)
+    todo = np.ones(n, dtype=bool)
+    while todo.any():
+        x[todo] = net(x[todo])
+        todo = x >= np.uint64(n)
+    return x.astype(np.int64)
+
+
+def greedy_batch(g, B: int, seed: int):
+    """B runs of the greedy algorithm (App. C.1), run b on ordering
+    ``feistel_order(n, b, seed)``.  Returns (Z n x B uint8, cuts int64[B])."""
+    Z = np.zeros((g.n, B), dtype=np.uint8)
+    for b in range(B):
+        Z[:, b] = greedy_maxcut(g, feistel_order(g.n, b, seed))
+    return Z, cut_values(g, Z)
+
+
+def flip_gains(g, Z) -> np.ndarray:
+    """Change of the cut when node v alone changes side, per column:
+    gain_v = sum_u w_vu s_u s_v with s = 1 - 2 z (the edges to same-side
+    neighbours become cut, the cut edges stop being cut)."""
+    S = 1.0 - 2.0 * np.asarray(Z, dtype=np.float64)
+    return S * (adjacency(g) @ S)
+
+
+def local_search(g, Z, max_rounds: int):
+    """1-flip local search on every column of Z (n x B, 0/1), at most
+    ``max_rounds`` rounds.  A round computes every gain and flips every node
+    whose gain is positive and beats the gain of each neighbour with a
+    positive gain (ties: the lower index wins); those nodes are pairwise
+    non-adjacent, so the cut grows by the sum of their gains.  Stops early
+    when no node has a positive gain (a 1-flip local optimum).  Returns
+    (Z', rounds that flipped at least one node).
+    """
+    Z = np.array(Z, dtype=np.uint8, copy=True)
+    # every (node v, neighbour u) pair of the adjacency
+    v = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    u = g.col_idx.astype(np.int64)
+    done = 0
+    for _ in range(max_rounds):
+        G = flip_gains(g, Z)
+        pos = G > 0
+        # u beats v in column c when G[u,c] > 0 and (G[u,c] > G[v,c] or (equal and u < v))
+        gu, gv = G[u], G[v]
+        beats = (gu > 0) & ((gu > gv) | ((gu == gv) & (u < v)[:, None]))
+        beaten = np.zeros_like(pos)
+        np.logical_or.at(beaten, v, beats)
+        flip = pos & ~beaten
+        if not flip.any():
+            break
+        Z[flip] ^= 1
+        done += 1
+    return Z, done
+

@@ -454,3 +454,103 @@ def test_greedy_half_guarantee():
         g = gg.er_graph(80, 0.1, seed)
         z = O.greedy_maxcut(g, np.random.default_rng(seed).permutation(g.n))
         assert 2 * O.cut_value(g, z) >= g.m
+
+
+# ------------------------------------------------ greedy comparator (App. C.1) and 1-flip local search
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 16, 17, 100, 1000])
+def test_feistel_order_is_a_permutation(n):
+    for b in range(3):
+        o = O.feistel_order(n, b, 12345)
+        assert sorted(o.tolist()) == list(range(n))
+
+
+def test_feistel_orders_differ_and_spread():
+    n, runs = 50, 400
+    first = np.array([O.feistel_order(n, b, 9)[0] for b in range(runs)])
+    # the first vertex of a run is close to uniform over the nodes
+    counts = np.bincount(first, minlength=n)
+    assert counts.max() < 5 * runs / n
+    assert len({tuple(O.feistel_order(n, b, 9)[:10]) for b in range(20)}) == 20
+
+
+def test_greedy_complete_graph_closed_form():
+    # identity order on K_n alternates sides: floor(n/2) * ceil(n/2) = max cut of K_n
+    for n in (2, 5, 8, 11):
+        u, v = np.triu_indices(n, 1)
+        g = gg.from_edges(n, u, v)
+        z = O.greedy_maxcut(g, np.arange(n))
+        assert O.cut_value(g, z) == (n // 2) * ((n + 1) // 2)
+
+
+def _signed(n, p, seed):
+    g = gg.er_graph(n, p, seed)
+    u, v, _ = g.edges()
+    w = np.random.default_rng(seed).choice([-2.0, -1.0, 1.0, 3.0], size=u.size)
+    return gg.from_edges(n, u, v, w)
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_flip_gain_is_the_cut_change_of_one_flip(signed):
+    g = _signed(30, 0.2, 2) if signed else gg.er_graph(30, 0.2, 2)
+    Z = (np.random.default_rng(3).random((g.n, 4)) < 0.5).astype(np.uint8)
+    G = O.flip_gains(g, Z)
+    base = O.cut_values(g, Z)
+    for v in range(g.n):
+        Zf = Z.copy()
+        Zf[v] ^= 1
+        np.testing.assert_array_equal(O.cut_values(g, Zf) - base, G[v].astype(np.int64))
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_local_search_rounds_flip_independent_sets_and_add_their_gains(signed):
+    g = _signed(80, 0.08, 4) if signed else gg.er_graph(80, 0.08, 4)
+    Z = (np.random.default_rng(5).random((g.n, 6)) < 0.5).astype(np.uint8)
+    u, v, _ = g.edges()
+    for _ in range(30):
+        G = O.flip_gains(g, Z)
+        Z1, r = O.local_search(g, Z, 1)
+        flipped = Z1 != Z
+        if r == 0:
+            assert not (G > 0).any() and not flipped.any()
+            break
+        assert not (flipped[u] & flipped[v]).any()                 # no two neighbours in one column
+        assert (G[flipped] > 0).all()
+        gain = np.where(flipped, G, 0).sum(axis=0).astype(np.int64)
+        np.testing.assert_array_equal(O.cut_values(g, Z1) - O.cut_values(g, Z), gain)
+        Z = Z1
+    else:
+        pytest.fail("local search did not converge in 30 rounds")
+
+
+def test_local_search_reaches_one_flip_optima_below_the_optimum():
+    for seed in range(3):
+        g = gg.er_graph(14, 0.35, 20 + seed)
+        opt, _ = O.brute_force_maxcut(g)
+        Z = (np.random.default_rng(seed).random((g.n, 16)) < 0.5).astype(np.uint8)
+        Z2, r = O.local_search(g, Z, 1000)
+        assert not (O.flip_gains(g, Z2) > 0).any()
+        assert (O.cut_values(g, Z2) <= opt).all() and (O.cut_values(g, Z2) >= O.cut_values(g, Z)).all()
+        Z3, r3 = O.local_search(g, Z2, 10)                          # a local optimum is left alone
+        assert r3 == 0 and np.array_equal(Z3, Z2)
+
+
+def test_one_flip_optima_are_fixed_points_of_the_multilinear_step():
+    # binaries with no improving single flip are the fixed points of the
+    # multilinear PGA step (F is affine in each coordinate)
+    g = gg.er_graph(40, 0.15, 6)
+    Z = (np.random.default_rng(7).random((g.n, 8)) < 0.5).astype(np.uint8)
+    Z, _ = O.local_search(g, Z, 1000)
+    Y = 2.0 * Z - 1.0
+    Yn, _ = O.pga_step(g, Y, 0.3, O.OBJ_MULTILINEAR01)
+    np.testing.assert_array_equal(Yn, Y)
+
+
+def test_solve_with_local_search_never_lowers_the_phase_cuts():
+    g = gg.er_graph(60, 0.1, 8)
+    sched = [O.Phase(1, 40, 0.01, 0.0), O.Phase(2, 10, 0.001, 0.0)]
+    a = O.solve(g, 16, sched, O.Params(init="idi"), 3)
+    b = O.solve(g, 16, sched[:1], O.Params(init="idi", local_search=50), 3)
+    # first phase identical up to the polish: every polished cut >= the raw cut
+    assert (b.phase_cuts[0] >= a.phase_cuts[0]).all()
+    assert b.best_cut == O.cut_value(g, b.assignment)
