@@ -426,6 +426,45 @@ def run_er4096_dense():
                          "algorithmic_flops_per_launch": flops}}
 
 
+def run_greedy_comparison():
+    """The paper's greedy comparison (App. C.1, Tables 5-6) on synthetic ER
+    graphs: ER(800, 0.06) and ER(5000, 0.002).  Greedy: B = 1024 runs on
+    random orderings, best of all; pDECO: IDI starts, B = 256, FP32,
+    2 x (800 unlifted alpha = 0.01 + 200 lifted l = 2 alpha = 0.001),
+    momentum 0.9, without and with the 1-flip local-search polish (at most
+    200 rounds per phase).  Device times (CUDA events)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    out = {}
+    sched = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)] * 2
+    for name, g in (("er800_p0.06", gg.er_graph(800, 0.06, 1)), ("er5000_p0.002", gg.er_graph(5000, 0.002, 9002))):
+        G = deco.graph_from(g)
+        rec = {"n": g.n, "m": g.m}
+        Bg = 1024
+        z = torch.zeros(g.n * Bg, dtype=torch.uint8, device="cuda")
+        cuts = torch.zeros(Bg, dtype=torch.int64, device="cuda")
+        deco.deco_greedy(G, 8, 1, z, cuts)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        deco.deco_greedy(G, Bg, 2, z, cuts)
+        e1.record()
+        torch.cuda.synchronize()
+        rec["greedy"] = {"runs": Bg, "best_cut": int(cuts.max().item()), "mean_cut": float(cuts.double().mean().item()),
+                         "device_s": e0.elapsed_time(e1) / 1e3}
+        for label, ls in (("pdeco", 0), ("pdeco_local_search", 200)):
+            p = deco.params(init=deco.DECO_INIT_IDI, local_search=ls)
+            deco.deco_solve(G, 256, [(1, 20, 0.01, 0.9)], p, 1, want_assignment=False, want_phase_cuts=False)
+            torch.cuda.synchronize()
+            e0.record()
+            r, _, _ = deco.deco_solve(G, 256, sched, p, 3, want_phase_cuts=False)
+            e1.record()
+            torch.cuda.synchronize()
+            rec[label] = {"best_cut": int(r.best_cut), "device_s": e0.elapsed_time(e1) / 1e3}
+        out[name] = rec
+    return out
+
+
 def run_ba256():
     """Batched workload: 256 Barabasi-Albert graphs (n ~ U{200..1200}, m = 4),
     B = 256 starts each, population of 32 (alpha, T) candidates x 8 starts,
@@ -627,6 +666,7 @@ def main():
     if rank == 0 and not args.main_only:
         extra["er1m_sparse"] = run_er1m()
         extra["er4096_dense"] = run_er4096_dense()
+        extra["greedy_comparison"] = run_greedy_comparison()
         extra["ba256_population"] = run_ba256()
         extra["learned_proposal"] = run_learned()
     if rank == 0:

@@ -294,7 +294,11 @@ typedef struct deco_params {
   float beta;                 /* IDI threshold (paper: 0.2) */
   float uniform_half_width;   /* DECO_INIT_UNIFORM half width (1 = full box) */
   int32_t kernel;             /* DECO_KERNEL_* selector, modifiers included */
-  int32_t reserved;
+  int32_t local_search;       /* deco_solve: at most this many rounds of the
+                                 1-flip local search (deco_local_search) on every
+                                 phase's rounded vectors before their cuts are
+                                 evaluated; 0 = off (the paper's method).  Not
+                                 available in deco_solve_batch. */
 } deco_params;
 
 int deco_init_block(const deco_graph* g, int32_t B, int32_t lift, int32_t ld,
@@ -438,6 +442,42 @@ int deco_mpnn_train_step(deco_mpnn* m, const deco_graph* g, const deco_batch* b,
  * before every step (one copy after the last step). */
 int deco_mpnn_train(deco_mpnn* m, const deco_graph* g, const deco_batch* b, const uint8_t* z,
                     uint64_t feat_seed, float lr, int32_t steps, double* losses, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Greedy comparator and 1-flip local search
+ * ------------------------------------------------------------------- */
+
+/* The greedy MaxCut algorithm the paper compares against (App. C.1): fix a
+ * vertex ordering, put the first vertex in S and every later vertex on the
+ * side that cuts more edges to the vertices already placed (ties: S).  Runs
+ * b = 0 .. B-1 in parallel, run b on the random ordering pi_b of [0, n): a
+ * balanced 4-round Feistel network on [0, 4^h) (4^h >= n, h >= 1) with round
+ * function word 0 of Philox4x32-10 counter (R, b, round, 6), key seed, and
+ * cycle walking onto [0, n).
+ *  z     device, n x B bytes row-major (z[v*B + b]), receives run b's sides
+ *        (1 = S).
+ *  cuts  device, B int64, receives every run's cut (Eq. 1).
+ * Stream-ordered, asynchronous (scratch: n x B int32 orderings).
+ * Errors: DECO_ERR_ARG, DECO_ERR_UNSUPPORTED (n >= 2^30), DECO_ERR_OOM, CUDA. */
+int deco_greedy(const deco_graph* g, int32_t B, uint64_t seed, uint8_t* z, int64_t* cuts, void* stream);
+
+/* 1-flip local search on B binary columns, in place.  A round computes the
+ * cut change of flipping each node alone, gain_v = sum_u w_vu s_u s_v
+ * (s = 1 - 2z), and flips every node whose gain is positive and larger than
+ * the gain of each neighbour with a positive gain (equal gains: the lower
+ * index wins); those nodes are pairwise non-adjacent, so every round raises
+ * the cut by the sum of their gains.  The search stops at a 1-flip local
+ * optimum (the binary fixed points of the multilinear step) or after
+ * max_rounds rounds.  No counterpart in the paper: a polish of the rounded
+ * vectors (deco_params.local_search applies it inside deco_solve).
+ *  z           device, n x B bytes row-major, 0/1; updated in place.
+ *  max_rounds  >= 0.
+ *  cuts        device, B int64, or NULL: the cuts after the search.
+ *  rounds      host int32 or NULL: the rounds that flipped at least one node
+ *              (when given, the call synchronises the stream).
+ * Errors: DECO_ERR_ARG, DECO_ERR_OOM, CUDA. */
+int deco_local_search(const deco_graph* g, int32_t B, uint8_t* z, int32_t max_rounds, int64_t* cuts,
+                      int32_t* rounds, void* stream);
 
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);

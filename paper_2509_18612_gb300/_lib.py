@@ -54,7 +54,8 @@ EXPORTED = [
     "deco_batch_graph", "deco_solve_batch", "deco_mpnn_create", "deco_mpnn_destroy", "deco_mpnn_num_params",
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
-    "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_last_error", "deco_abi_version",
+    "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_greedy", "deco_local_search",
+    "deco_last_error", "deco_abi_version",
 ]
 
 
@@ -76,7 +77,7 @@ class deco_params(ctypes.Structure):
                 ("init", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
                 ("eta", ctypes.c_float), ("scale", ctypes.c_float), ("beta", ctypes.c_float),
                 ("uniform_half_width", ctypes.c_float), ("kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("local_search", ctypes.c_int32)]
 
 
 class deco_phase(ctypes.Structure):
@@ -133,6 +134,8 @@ def _load():
         "deco_dui_mean": (ctypes.c_int, [P, U64, I32, P, P]),
         "deco_solve": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_phase), I32, ctypes.POINTER(deco_params),
                                       U64, P, P, P, P, P, ctypes.POINTER(deco_result)]),
+        "deco_greedy": (ctypes.c_int, [P, I32, U64, P, P, P]),
+        "deco_local_search": (ctypes.c_int, [P, I32, P, I32, P, P, P]),
         "deco_last_error": (ctypes.c_char_p, []),
         "deco_abi_version": (ctypes.c_int, []),
     }
@@ -249,6 +252,19 @@ def deco_eval_cuts(g: Graph, B: int, z_dev, cuts_dev, stream=None):
     _check(lib.deco_eval_cuts(g, int(B), _ptr(z_dev), _ptr(cuts_dev), _stream(stream)))
 
 
+def deco_greedy(g: Graph, B: int, seed: int, z_dev, cuts_dev, stream=None):
+    """Greedy comparator (App. C.1): B runs on Feistel orderings; z_dev n x B uint8, cuts_dev B int64."""
+    _check(lib.deco_greedy(g, int(B), int(seed), _ptr(z_dev), _ptr(cuts_dev), _stream(stream)))
+
+
+def deco_local_search(g: Graph, B: int, z_dev, max_rounds: int, cuts_dev=None, stream=None) -> int:
+    """1-flip local search in place on z_dev (n x B uint8); returns the rounds that flipped a node."""
+    r = ctypes.c_int32(0)
+    _check(lib.deco_local_search(g, int(B), _ptr(z_dev), int(max_rounds), _ptr(cuts_dev), ctypes.byref(r),
+                                 _stream(stream)))
+    return int(r.value)
+
+
 def step_args(objective=DECO_OBJ_MULTILINEAR01, precision=DECO_PREC_FP32, alpha=0.01, momentum=0.0,
               alpha_cols=None, steps_cols=None, t=0) -> deco_step_args:
     return deco_step_args(objective, precision, alpha, momentum, _ptr(alpha_cols), _ptr(steps_cols), t, 0)
@@ -297,9 +313,9 @@ def deco_round_cut(g: Graph, B: int, lift: int, ld: int, precision: int, y, zbit
 
 def params(objective=DECO_OBJ_MULTILINEAR01, precision=DECO_PREC_FP32, init=DECO_INIT_UNIFORM,
            polish_steps=0, eta=0.8, scale=1e-4, beta=0.2, uniform_half_width=1.0,
-           kernel=DECO_KERNEL_AUTO) -> deco_params:
+           kernel=DECO_KERNEL_AUTO, local_search=0) -> deco_params:
     return deco_params(objective, precision, init, polish_steps, eta, scale, beta, uniform_half_width,
-                       kernel, 0)
+                       kernel, local_search)
 
 
 def deco_init_block(g: Graph, B: int, lift: int, ld: int, p: deco_params, seed: int, phase: int, y,

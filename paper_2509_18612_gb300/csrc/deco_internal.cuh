@@ -107,7 +107,7 @@ __device__ __forceinline__ float box_muller(uint32_t a, uint32_t b) {
   return r * cospif(2.0f * u01(b));
 }
 
-enum RngStream : uint32_t { STREAM_INIT = 0, STREAM_IDI = 1, STREAM_DUI = 2, STREAM_EVOLVE = 3 };
+enum RngStream : uint32_t { STREAM_INIT = 0, STREAM_IDI = 1, STREAM_DUI = 2, STREAM_EVOLVE = 3, STREAM_ORDER = 6 };
 
 // bf16 <-> fp32 packing of a 32-bit word holding two bf16 values (low half first).
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
@@ -149,6 +149,10 @@ int launch_cut_bits(const deco_graph* g, int32_t B, const uint32_t* zbits, int64
 int launch_cut_bytes(const deco_graph* g, int32_t B, const uint8_t* z, int64_t* cuts,
                      cudaStream_t st);
 int launch_argmax(int32_t B, const int64_t* cuts, int32_t* best, cudaStream_t st);
+// 1-flip local search on bit-packed columns (n x ceil(B/32) words), in place;
+// gains: n x 32 ceil(B/32) int32 scratch, changed: max_rounds + 1 int32 scratch
+int launch_local_search(const deco_graph* g, int32_t B, uint32_t* zbits, int32_t max_rounds, int32_t* gains,
+                        int32_t* changed, cudaStream_t st);
 
 // Phase bookkeeping of deco_solve: best of the phase, global best record.
 struct BestRecord {

@@ -48,6 +48,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
   if (B < 1 || n_phases < 1 || n_phases > 64) { set_error("need B >= 1 and 1 <= n_phases <= 64"); return DECO_ERR_ARG; }
   if ((rc = check_prec(p->precision)) || (rc = check_obj(p->objective))) return rc;
   if (!valid_selector(p->kernel)) { set_error("bad kernel selector 0x%x", p->kernel); return DECO_ERR_ARG; }
+  if (p->local_search < 0) { set_error("local_search must be >= 0"); return DECO_ERR_ARG; }
   int32_t max_lift = 1;
   bool any_mom = false;
   for (int k = 0; k < n_phases; ++k) {
@@ -102,6 +103,13 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
     if ((rc = s.alloc(&pbz, (size_t)n)) || (rc = s.alloc(&bz, (size_t)n))) return rc;
     if ((rc = s.alloc(&h, sizeof(float) * n)) || (rc = s.alloc(&side, (size_t)n))) return rc;
     if ((rc = s.alloc(&flag, sizeof(int32_t)))) return rc;
+    int32_t* ls_gains = nullptr;
+    int32_t* ls_changed = nullptr;
+    if (p->local_search > 0) {
+      if ((rc = s.alloc(&ls_gains, sizeof(int32_t) * (size_t)n * 32 * W)) ||
+          (rc = s.alloc(&ls_changed, sizeof(int32_t) * ((size_t)p->local_search + 1))))
+        return rc;
+    }
 
     cudaEvent_t ev0, ev1;
     DECO_CUDA_TRY(cudaEventCreate(&ev0));
@@ -192,6 +200,11 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
       edge_updates += g->nnz * (int64_t)C * ph.steps;
       int64_t* pc = cuts + (size_t)k * B;
       if ((rc = launch_pack(g, B, ph.lift, ld, prec, ybuf[cur], zbits, st))) return rc;
+      if (p->local_search > 0) {
+        // 1-flip polish of the rounded vectors (off by default)
+        if ((rc = launch_local_search(g, B, zbits, p->local_search, ls_gains, ls_changed, st))) return rc;
+        kernels += 2 * (int64_t)p->local_search;
+      }
       if ((rc = launch_cut_bits(g, B, zbits, pc, st))) return rc;
       if ((rc = launch_phase_finish(g, B, k, pc, zbits, best_idx + k, rec, pbz, bz, st))) return rc;
       kernels += 5;   // pack, cut, argmax, record, extract
