@@ -465,6 +465,65 @@ def run_greedy_comparison():
     return out
 
 
+def run_lifting_sweep():
+    """Lifting ablation (the paper's Table 2): pLUCO with l = 1, 2, 3, 4, 8 on
+    the config-2 ER graph (ER(800, 0.06), B = 256, T = 1000, alpha = 0.001,
+    momentum 0.9, IDI) and on the dense config-4 graph (ER(4096, 0.5),
+    B = 128, T = 500, alpha = 1e-4, BF16, l = 1, 2, 4).  Best cut, device
+    time and edge-updates/s of every l (C = B l columns)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    out = {}
+    cases = (("er800_p0.06", gg.er_graph(800, 0.06, 1), 256, 1000, 0.001, deco.DECO_PREC_FP32, (1, 2, 3, 4, 8)),
+             ("er4096_p0.5", gg.er_graph(DENSE_N, DENSE_P, DENSE_N), 128, 500, 1e-4, deco.DECO_PREC_BF16, (1, 2, 4)))
+    for name, g, Bl, T, alpha, prec, lifts in cases:
+        G = deco.graph_from(g)
+        rows = {}
+        for l in lifts:
+            if prec == deco.DECO_PREC_BF16:
+                deco.deco_autotune(G, Bl * l, prec, deco.DECO_OBJ_MULTILINEAR01, 0.9, 10)
+            p = deco.params(init=deco.DECO_INIT_IDI, precision=prec)
+            sched = [(l, T, alpha, 0.9)]
+            deco.deco_solve(G, Bl, [(l, 10, alpha, 0.9)], p, 1, want_assignment=False, want_phase_cuts=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r, _, _ = deco.deco_solve(G, Bl, sched, p, 4, want_phase_cuts=False)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            rows[f"l{l}"] = {"best_cut": int(r.best_cut), "device_s": t, "edge_updates_per_s": r.edge_updates / t}
+        out[name] = {"B": Bl, "T": T, "alpha": alpha, "precision": "bf16" if prec else "fp32", "lifts": rows}
+    return out
+
+
+def run_init_ablation():
+    """Initialisation ablation (Sec. 4.1-4.2) on synthetic stand-ins for the
+    Gset graphs the paper reports (G14: n = 800, m = 4694; G22: n = 2000,
+    m = 19990; G55: n = 5000, m = 12498), ER with the same n and expected m:
+    pDECO (B = 256, 2 x (800 + 200 lifted) steps, momentum 0.9, FP32) from
+    uniform, DUI, IDI and IDI + uniform starts.  Best cut and the mean cut of
+    the first phase's rounded starts."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+    sched = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)] * 2
+    inits = (("uniform", deco.DECO_INIT_UNIFORM), ("dui", deco.DECO_INIT_DUI), ("idi", deco.DECO_INIT_IDI),
+             ("idi_half_uniform", deco.DECO_INIT_IDI_HALF_UNIFORM))
+    out = {}
+    for name, n, m in (("g14_like", 800, 4694), ("g22_like", 2000, 19990), ("g55_like", 5000, 12498)):
+        g = gg.er_graph(n, m / (n * (n - 1) / 2), 14000 + n)
+        G = deco.graph_from(g)
+        rec = {"n": g.n, "m": g.m}
+        for label, init in inits:
+            p = deco.params(init=init)
+            r, _, pc = deco.deco_solve(G, 256, sched, p, 6)
+            torch.cuda.synchronize()
+            rec[label] = {"best_cut": int(r.best_cut), "phase0_mean_cut": float(pc[0].mean()),
+                          "phase0_best_cut": int(pc[0].max())}
+        out[name] = rec
+    return out
+
+
 def run_ba256():
     """Batched workload: 256 Barabasi-Albert graphs (n ~ U{200..1200}, m = 4),
     B = 256 starts each, population of 32 (alpha, T) candidates x 8 starts,
@@ -667,6 +726,8 @@ def main():
         extra["er1m_sparse"] = run_er1m()
         extra["er4096_dense"] = run_er4096_dense()
         extra["greedy_comparison"] = run_greedy_comparison()
+        extra["lifting_sweep"] = run_lifting_sweep()
+        extra["init_ablation"] = run_init_ablation()
         extra["ba256_population"] = run_ba256()
         extra["learned_proposal"] = run_learned()
     if rank == 0:

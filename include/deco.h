@@ -348,6 +348,29 @@ int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t
                const deco_params* p, uint64_t seed, const float* x0, const float* mean,
                uint8_t* assignment, int64_t* phase_cuts, void* stream, deco_result* out);
 
+/* pDECO under a time budget (Alg. 3: the schedule is repeated until the
+ * time budget expires), resumable.  Repetition r runs deco_solve with seed
+ * + r; repetition 0 starts as p->init says, or, when `warm` is given, from
+ * Gaussian starts around 2 warm - 1; every later repetition starts around
+ * 2 z* - 1 of the best vector found so far (DECO_INIT_MEAN, Sec. 4.2).  The
+ * call returns after the first repetition whose end brings the summed device
+ * time to budget_ms or more, or after max_repeats repetitions.
+ *  budget_ms    >= 0 (0: one repetition).
+ *  max_repeats  >= 1.
+ *  warm         host, n bytes 0/1, or NULL: resume from this assignment (the
+ *               assignment of an earlier call); its cut is the best so far.
+ *  assignment   host, n bytes or NULL: the best assignment found.
+ *  repeats      host int32 or NULL: repetitions run.
+ *  out          best cut over the warm start and all repetitions (best_init /
+ *               best_phase of the repetition that found it, -1 if the warm
+ *               start stayed best); edge_updates, device_ms and
+ *               kernel_launches summed over the repetitions.
+ * Synchronous.  Errors: as deco_solve. */
+int deco_solve_budget(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t n_phases,
+                      const deco_params* p, uint64_t seed, double budget_ms, int32_t max_repeats,
+                      const uint8_t* warm, uint8_t* assignment, int32_t* repeats, void* stream,
+                      deco_result* out);
+
 /* ---------------------------------------------------------------- batches
  * Many graphs solved together with the evolution-based hyper-parameter
  * search of Sec. 4.3.  A batch is the disjoint union of its graphs (a

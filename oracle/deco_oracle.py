@@ -501,6 +501,23 @@ def solve(g, B: int, phases: Sequence[Phase], params: Params, seed: int, x0=None
                        final_Y=Y if keep_final else None)
 
 
+def solve_repeated(g, B: int, phases: Sequence[Phase], params: Params, seed: int, repeats: int, warm=None):
+    """pDECO repeated ``repeats`` times (Alg. 3 repeats its schedule until the
+    time budget expires; here the budget is a number of repetitions).
+    Repetition r solves with seed + r; it starts as ``params.init`` says, or
+    around 2 z* - 1 (init "mean") once a best vector z* exists (the warm
+    start, or an earlier repetition's best).  Returns (best cut, best z)."""
+    from dataclasses import replace
+    best_z = None if warm is None else np.asarray(warm, dtype=np.uint8).copy()
+    best_cut = -1 if warm is None else cut_value(g, best_z)
+    for r in range(repeats):
+        p = params if best_z is None else replace(params, init="mean", mean=2.0 * best_z.astype(np.float64) - 1.0)
+        res = solve(g, B, phases, p, seed + r)
+        if res.best_cut > best_cut:
+            best_cut, best_z = res.best_cut, res.assignment.copy()
+    return best_cut, best_z
+
+
 # ----------------------------------------------------------------------------
 # Evolution-based hyper-parameter search (Sec. 4.3)
 # ----------------------------------------------------------------------------

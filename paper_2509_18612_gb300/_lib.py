@@ -54,7 +54,7 @@ EXPORTED = [
     "deco_batch_graph", "deco_solve_batch", "deco_mpnn_create", "deco_mpnn_destroy", "deco_mpnn_num_params",
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
-    "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_greedy", "deco_local_search",
+    "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_solve_budget", "deco_greedy", "deco_local_search",
     "deco_last_error", "deco_abi_version",
 ]
 
@@ -134,6 +134,8 @@ def _load():
         "deco_dui_mean": (ctypes.c_int, [P, U64, I32, P, P]),
         "deco_solve": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_phase), I32, ctypes.POINTER(deco_params),
                                       U64, P, P, P, P, P, ctypes.POINTER(deco_result)]),
+        "deco_solve_budget": (ctypes.c_int, [P, I32, ctypes.POINTER(deco_phase), I32, ctypes.POINTER(deco_params),
+                                             U64, ctypes.c_double, I32, P, P, P, P, ctypes.POINTER(deco_result)]),
         "deco_greedy": (ctypes.c_int, [P, I32, U64, P, P, P]),
         "deco_local_search": (ctypes.c_int, [P, I32, P, I32, P, P, P]),
         "deco_last_error": (ctypes.c_char_p, []),
@@ -250,6 +252,21 @@ def deco_eval_cut(g: Graph, z) -> int:
 
 def deco_eval_cuts(g: Graph, B: int, z_dev, cuts_dev, stream=None):
     _check(lib.deco_eval_cuts(g, int(B), _ptr(z_dev), _ptr(cuts_dev), _stream(stream)))
+
+
+def deco_solve_budget(g: Graph, B: int, phases: Sequence, p: deco_params, seed: int, budget_ms: float,
+                      max_repeats: int = 1 << 30, warm=None, stream=None):
+    """pDECO repeated until budget_ms of device time (or max_repeats); returns
+    (deco_result, best assignment uint8[n], repetitions run)."""
+    arr = (deco_phase * len(phases))(*[deco_phase(int(l), int(s), float(a), float(m)) for l, s, a, m in phases])
+    assignment = np.zeros(g.n, dtype=np.uint8)
+    warm_p = None if warm is None else np.ascontiguousarray(warm, dtype=np.uint8)
+    out = deco_result()
+    reps = ctypes.c_int32(0)
+    _check(lib.deco_solve_budget(g, int(B), arr, len(phases), ctypes.byref(p), int(seed), float(budget_ms),
+                                 int(max_repeats), _ptr(warm_p), _ptr(assignment), ctypes.byref(reps),
+                                 _stream(stream), ctypes.byref(out)))
+    return out, assignment, int(reps.value)
 
 
 def deco_greedy(g: Graph, B: int, seed: int, z_dev, cuts_dev, stream=None):

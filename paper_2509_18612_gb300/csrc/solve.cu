@@ -241,3 +241,62 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
   out->kernel_launches = kernels;
   return DECO_OK;
 }
+
+extern "C" int deco_solve_budget(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t n_phases,
+                                 const deco_params* p, uint64_t seed, double budget_ms, int32_t max_repeats,
+                                 const uint8_t* warm, uint8_t* assignment, int32_t* repeats, void* stream,
+                                 deco_result* out) {
+  clear_error();
+  int rc = check_graph(g);
+  if (rc) return rc;
+  if (!p || !out || !phases) { set_error("NULL argument"); return DECO_ERR_ARG; }
+  if (max_repeats < 1 || !(budget_ms >= 0.0)) { set_error("need max_repeats >= 1 and budget_ms >= 0"); return DECO_ERR_ARG; }
+  const int32_t n = g->n;
+  std::vector<uint8_t> best_z((size_t)n, 0), z((size_t)n, 0);
+  std::vector<float> mean((size_t)n, 0.0f);
+  deco_result total{};
+  total.best_cut = -1;   // below any cut: the first repetition always records its best
+  total.best_init = -1;
+  total.best_phase = -1;
+  bool have_best = false;
+  if (warm) {
+    for (int32_t v = 0; v < n; ++v) best_z[v] = warm[v] ? 1 : 0;
+    if ((rc = deco_eval_cut(g, best_z.data(), &total.best_cut))) return rc;
+    have_best = true;
+  }
+  int32_t r = 0;
+  double used = 0.0;
+  for (; r < max_repeats; ++r) {
+    deco_params pr = *p;
+    const float* m = nullptr;
+    if (have_best) {
+      // Gaussian starts around 2 z* - 1 of the best vector so far (Sec. 4.2)
+      for (int32_t v = 0; v < n; ++v) mean[v] = best_z[v] ? 1.0f : -1.0f;
+      pr.init = DECO_INIT_MEAN;
+      m = mean.data();
+    }
+    deco_result res{};
+    if ((rc = deco_solve(g, B, phases, n_phases, &pr, seed + (uint64_t)r, nullptr, m, z.data(), nullptr, stream,
+                         &res)))
+      return rc;
+    if (res.best_cut > total.best_cut) {   // strictly better: earlier repetitions win ties
+      total.best_cut = res.best_cut;
+      total.best_init = res.best_init;
+      total.best_phase = res.best_phase;
+      best_z = z;
+    }
+    have_best = true;
+    total.edge_updates += res.edge_updates;
+    total.device_ms += res.device_ms;
+    total.kernel_launches += res.kernel_launches;
+    used += res.device_ms;
+    if (used >= budget_ms) {
+      ++r;
+      break;
+    }
+  }
+  if (assignment) std::copy(best_z.begin(), best_z.end(), assignment);
+  if (repeats) *repeats = r;
+  *out = total;
+  return DECO_OK;
+}

@@ -122,3 +122,28 @@ def test_greedy_and_local_search_at_eval_size():
     assert r == rr
     np.testing.assert_array_equal(z.cpu().numpy().reshape(g.n, B), Zr)
     assert (cuts.cpu().numpy() >= O.cut_values(g, Zg)).all()
+
+
+def test_budget_solve_repetitions_match_oracle():
+    g = gg.er_graph(100, 0.1, 0)
+    G = deco.graph_from(g)
+    sched = [(1, 200, 0.01, 0.9), (2, 50, 0.001, 0.9)]
+    p = deco.params(init=deco.DECO_INIT_IDI)
+    res, z, reps = deco.deco_solve_budget(G, 64, sched, p, 21, budget_ms=1e9, max_repeats=3)
+    assert reps == 3
+    cut, zr = O.solve_repeated(g, 64, [O.Phase(*s) for s in sched], O.Params(init="idi"), 21, 3)
+    assert res.best_cut == cut == O.cut_value(g, z)
+
+
+def test_budget_solve_stops_on_time_and_resumes():
+    g = gg.er_graph(800, 0.06, 1)
+    G = deco.graph_from(g)
+    sched = [(1, 100, 0.01, 0.9)]
+    p = deco.params(init=deco.DECO_INIT_IDI)
+    r0, z0, n0 = deco.deco_solve_budget(G, 128, sched, p, 5, budget_ms=0.0)
+    assert n0 == 1 and r0.best_cut == O.cut_value(g, z0)
+    r1, z1, n1 = deco.deco_solve_budget(G, 128, sched, p, 6, budget_ms=5.0, max_repeats=1000)
+    assert 1 <= n1 < 1000 and r1.device_ms >= 5.0
+    # resume from the first call's assignment: never below it
+    r2, z2, n2 = deco.deco_solve_budget(G, 128, sched, p, 7, budget_ms=0.0, warm=z0)
+    assert r2.best_cut >= r0.best_cut and r2.best_cut == O.cut_value(g, z2)

@@ -554,3 +554,14 @@ def test_solve_with_local_search_never_lowers_the_phase_cuts():
     # first phase identical up to the polish: every polished cut >= the raw cut
     assert (b.phase_cuts[0] >= a.phase_cuts[0]).all()
     assert b.best_cut == O.cut_value(g, b.assignment)
+
+
+def test_repeated_solve_keeps_an_optimal_warm_start_and_never_loses_ground():
+    g = gg.er_graph(14, 0.35, 31)
+    opt, zopt = O.brute_force_maxcut(g)
+    sched = [O.Phase(1, 30, 0.01, 0.0)]
+    cut, z = O.solve_repeated(g, 4, sched, O.Params(init="idi"), 2, 2, warm=zopt)
+    assert cut == opt and O.cut_value(g, z) == opt
+    c1, _ = O.solve_repeated(g, 4, sched, O.Params(init="idi"), 2, 1)
+    c3, z3 = O.solve_repeated(g, 4, sched, O.Params(init="idi"), 2, 3)
+    assert opt >= c3 >= c1 and O.cut_value(g, z3) == c3
