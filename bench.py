@@ -129,6 +129,20 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def whole_job(ms_local: float, units_per_rank: float, world: int, device="cpu"):
+    """Timed milliseconds as the maximum over the ranks (replicas run the same
+    work), and the whole-job rate: the units every rank processed / that time."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, units_per_rank * world / (ms / 1e3)
+
+
 def run_deco(args, rank, world):
     import torch
     import paper_2509_18612_gb300 as deco
@@ -180,15 +194,7 @@ def run_deco(args, rank, world):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     timed_launches = launches[0]
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    units = edge_updates(gs) * args.steps * world
-    value = units / (ms / 1e3)
+    ms, value = whole_job(sum(a.elapsed_time(b) for a, b in ev), edge_updates(gs) * args.steps, world, dev)
 
     # ---- end to end through the public API with host buffers
     e2e = None
