@@ -1,0 +1,142 @@
+"""Parity at the workloads' full sizes, in the launch shapes the benchmark
+times (the autotuner's choice for every block shape), on outputs the oracle
+can compute one by one:
+
+  * config 2 (ER(800, 0.06) and the 40 x 20 torus, B = 1024, pDECO T = 2000):
+    the first phase's starting points are independent, so the oracle runs a
+    sample of 128 of them per graph through the 800 unlifted steps; rounded
+    cuts identical on >= 99 % of the sampled (graph, start) pairs;
+  * config 3 (256 BA graphs, B = 256, population 32 x 8): the first round's
+    columns are independent given the seeded population, so the oracle runs
+    64 sampled columns of four graphs; >= 99 % identical;
+  * config 4 sparse (ER, n = 10^6, average degree 10, B = 128, BF16): the IDI
+    mean bit-exact in full; one step from a dyadic block (every partial sum
+    exact in FP32) on 1024 sampled rows within one bf16 rounding; rounding and
+    cuts of that block bit-exact in full;
+  * config 5 (BA(2000, 4), ER(5000, 0.002)): the network's proposal within
+    1e-5 of the oracle's at every node.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+from oracle import deco_oracle as O
+from oracle import mpnn_oracle as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2509_18612_gb300 as deco  # noqa: E402
+
+DEV = torch.device("cuda:0")
+MUL = deco.DECO_OBJ_MULTILINEAR01
+
+
+def test_config2_first_phase_sampled_starts():
+    sched = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)] * 2
+    B, same, total = 1024, 0, 0
+    for g, seed in ((gg.er_graph(800, 0.06, 1), 11), (gg.torus_graph(40, 20, 2), 12)):
+        G = deco.graph_from(g)
+        for C in (B, 2 * B):
+            deco.deco_autotune(G, C, deco.DECO_PREC_FP32, MUL, 0.9, 10)
+        res, z, pc = deco.deco_solve(G, B, sched, deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM), seed)
+        assert res.best_cut == O.cut_value(g, z)
+        cols = np.sort(np.random.default_rng(seed).choice(B, 128, replace=False))
+        Y0 = O.initial_block(g, B, 1, O.Params(init="idi_half_uniform"), seed)[:, cols]
+        Y = O.run_phase(g, Y0, O.Phase(*sched[0]), O.OBJ_MULTILINEAR01)
+        cuts = O.cut_values(g, O.binarize(Y, 1))
+        same += int(np.sum(cuts == pc[0][cols]))
+        total += cols.size
+    assert same >= 0.99 * total, (same, total)
+
+
+def test_config3_first_round_sampled_columns():
+    rng = np.random.default_rng(3000)
+    sizes = rng.integers(200, 1201, 256)
+    graphs = [gg.ba_graph(int(n), 4, 3000 + i) for i, n in enumerate(sizes)]
+    batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs])
+    U = batch.graph()
+    for C in (256, 512):
+        deco.deco_autotune(U, C, deco.DECO_PREC_FP32, MUL, 0.9, 10)
+    B, P, seed = 256, 32, 2
+    pop = deco.population(candidates=P, rounds=5, t_lo=500, t_hi=2000, e_lo=-4.0, e_hi=-1.0, momentum=0.9,
+                          lifts=(1, 2))
+    p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM)
+    res, best, ex = deco.deco_solve_batch(batch, B, p, pop, seed, want_round_cuts=True)
+    e, T = O.population_init(P, 500, 2000, -4.0, -1.0, seed)
+    per = B // P
+    cand = np.arange(B) // per
+    same = total = 0
+    for gi in (0, 17, 128, 255):
+        g = graphs[gi]
+        cols = np.sort(np.random.default_rng(gi).choice(B, 64, replace=False))
+        Y0 = O.initial_block(g, B, 1, O.Params(init="idi_half_uniform"), seed + gi)[:, cols]
+        alpha_cols = O.alpha_of(e)[cand[cols]]
+        steps_cols = T[cand[cols]]
+        Y = O.run_phase(g, Y0, O.Phase(1, int(steps_cols.max()), 0.0, 0.9), O.OBJ_MULTILINEAR01,
+                        alpha_cols=alpha_cols, active_steps=steps_cols)
+        cuts = O.cut_values(g, O.binarize(Y, 1))
+        same += int(np.sum(cuts == ex["round_cuts"][0][gi][cols]))
+        total += cols.size
+    assert same >= 0.99 * total, (same, total)
+
+
+@pytest.fixture(scope="module")
+def er1m():
+    g = gg.er_graph_avg_degree(1_000_000, 10, 4)
+    return g, deco.graph_from(g)
+
+
+def test_config4_sparse_idi_mean_full(er1m):
+    g, G = er1m
+    h = torch.zeros(g.n, device=DEV)
+    deco.deco_idi_mean(G, 0.2, 5, 0, h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(h.cpu().numpy().astype(np.float64), O.idi_mean(g, 5, 0))
+
+
+def test_config4_sparse_step_and_cuts(er1m):
+    g, G = er1m
+    C = 128
+    sel, _ = deco.deco_autotune(G, C, deco.DECO_PREC_BF16, MUL, 0.0, 5)
+    rng = np.random.default_rng(8)
+    Yd = (rng.integers(-64, 65, size=(g.n, C)) / 64.0).astype(np.float32)   # dyadic: exact sums
+    y = torch.from_numpy(Yd).to(DEV).to(torch.bfloat16)
+    # rounding and integer cuts of the seeded block, in full
+    zbits = torch.zeros(g.n * (C // 32), dtype=torch.int32, device=DEV)
+    cuts = torch.zeros(C, dtype=torch.int64, device=DEV)
+    best = torch.zeros(1, dtype=torch.int32, device=DEV)
+    deco.deco_round_cut(G, C, 1, C, deco.DECO_PREC_BF16, y, zbits, cuts, best)
+    torch.cuda.synchronize()
+    Zd = O.binarize(Yd, 1)
+    ref_cuts = np.concatenate([O.cut_values(g, Zd[:, c:c + 16]) for c in range(0, C, 16)])
+    np.testing.assert_array_equal(cuts.cpu().numpy(), ref_cuts)
+    assert int(best.item()) == O.best_of(ref_cuts)
+    # one step in the tuned shape, 1024 sampled rows against the definition
+    a = deco.step_args(MUL, deco.DECO_PREC_BF16, 0.01, 0.0)
+    flag = torch.zeros(1, dtype=torch.int32, device=DEV)
+    deco.deco_run_phase(G, C, C, y, None, 1, a, sel, flag)
+    torch.cuda.synchronize()
+    assert int(flag.item()) == 0
+    rows = np.sort(np.random.default_rng(9).choice(g.n, 1024, replace=False))
+    A = O.adjacency(g)
+    X = (1.0 + Yd.astype(np.float64)) / 2.0
+    d = O.net_degree(g)
+    Gr = d[rows, None] - 2.0 * (A[rows] @ X)
+    ref = 2.0 * np.clip(X[rows] + 0.01 * Gr, 0.0, 1.0) - 1.0
+    out = y[torch.from_numpy(rows).to(DEV)].float().cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(out - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6)
+
+
+@pytest.mark.parametrize("which", ["ba2000", "er5000"])
+def test_config5_proposal_full(which):
+    g = gg.ba_graph(2000, 4, 9001) if which == "ba2000" else gg.er_graph(5000, 0.002, 9002)
+    m = deco.Mpnn(64, 3, 77)
+    h = torch.zeros(g.n, device=DEV)
+    m.infer(deco.graph_from(g), h, feat_seed=7)
+    torch.cuda.synchronize()
+    o, _ = M.forward(m.get_params().astype(np.float64), g, M.features(g, 7))
+    np.testing.assert_allclose(h.cpu().numpy(), np.tanh(o), rtol=0, atol=1e-5)
