@@ -12,8 +12,9 @@
 //   loss per graph: min over the two labellings z, 1 - z of the mean
 //   logistic loss softplus(-t o), t = 2z - 1 (a cut does not change when
 //   both sides swap); batch loss = mean over graphs.
-// Weight gradients are reductions over nodes done by one thread per output
-// entry in node order, so they are deterministic.
+// Weight gradients are reductions over nodes in a fixed order (chunks of
+// nodes in node order, then the chunks in order), so they are deterministic.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -216,22 +217,52 @@ __global__ void k_loss_dout(int32_t n, int32_t n_graphs, const float* o, const u
   dout[v] = (float)(-s * t * sigmoid_d(-s * t * (double)o[v]) / (ng * (double)n_graphs));
 }
 
-// dW[i][j] = sum_v in[v][i] d[v][j] (node order, one thread per entry)
-__global__ void k_wgrad(int32_t n, int32_t F, int32_t H, const float* in, const float* d, float* dW) {
-  const int32_t i = blockIdx.x, j = threadIdx.x;
-  if (j >= H) return;
-  float acc = 0.0f;
-  for (int32_t v = 0; v < n; ++v) acc = fmaf(in[(size_t)v * F + i], d[(size_t)v * H + j], acc);
-  dW[(size_t)i * H + j] = acc;
+// Weight gradients dW[i][j] = sum_v in[v][i] d[v][j] (in == NULL: in = 1, the
+// bias gradient) as a two-level reduction with a fixed order: chunks of
+// WG_CHUNK nodes summed in node order, then the chunks summed in chunk order.
+constexpr int WG_CHUNK = 256, WG_TILE = 32, WG_THREADS = 256, WG_PER = 16;
+
+__global__ void __launch_bounds__(WG_THREADS) k_wgrad_part(int32_t n, int32_t F, int32_t H, const float* in,
+                                                            const float* d, float* part) {
+  extern __shared__ float tile[];   // WG_TILE x (F + H)
+  const int32_t c = blockIdx.x;
+  const int32_t v0 = c * WG_CHUNK, v1 = min(n, v0 + WG_CHUNK);
+  const int32_t FH = F * H;
+  float* tin = tile;
+  float* td = tile + WG_TILE * F;
+  for (int32_t e0 = 0; e0 < FH; e0 += WG_THREADS * WG_PER) {
+    float acc[WG_PER];
+#pragma unroll
+    for (int k = 0; k < WG_PER; ++k) acc[k] = 0.0f;
+    for (int32_t t0 = v0; t0 < v1; t0 += WG_TILE) {
+      const int32_t cnt = min(WG_TILE, v1 - t0);
+      __syncthreads();
+      for (int32_t x = threadIdx.x; x < cnt * F; x += WG_THREADS)
+        tin[x] = in ? in[(size_t)t0 * F + x] : 1.0f;
+      for (int32_t x = threadIdx.x; x < cnt * H; x += WG_THREADS) td[x] = d[(size_t)t0 * H + x];
+      __syncthreads();
+      for (int32_t r = 0; r < cnt; ++r) {
+#pragma unroll
+        for (int k = 0; k < WG_PER; ++k) {
+          const int32_t e = e0 + k * WG_THREADS + threadIdx.x;
+          if (e < FH) acc[k] = fmaf(tin[r * F + e / H], td[r * H + e % H], acc[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < WG_PER; ++k) {
+      const int32_t e = e0 + k * WG_THREADS + threadIdx.x;
+      if (e < FH) part[(size_t)c * FH + e] = acc[k];
+    }
+  }
 }
 
-// db[j] = sum_v d[v][j]
-__global__ void k_bgrad(int32_t n, int32_t H, const float* d, float* db) {
-  const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= H) return;
+__global__ void k_wgrad_sum(int32_t chunks, int32_t FH, const float* part, float* dW) {
+  const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= FH) return;
   float acc = 0.0f;
-  for (int32_t v = 0; v < n; ++v) acc += d[(size_t)v * H + j];
-  db[j] = acc;
+  for (int32_t c = 0; c < chunks; ++c) acc += part[(size_t)c * FH + e];
+  dW[e] = acc;
 }
 
 __global__ void k_relu_mask(int64_t count, const float* pre, float* dh) {
@@ -332,6 +363,19 @@ int forward(const deco_mpnn* m, const deco_graph* g, const FeatureInfo& fi, uint
   return DECO_OK;
 }
 
+// dW (F x H) = in^T d over all n nodes (in == NULL: the column sums of d); part: chunk scratch
+int wgrad(int32_t n, int32_t F, int32_t H, const float* in, const float* d, float* part, float* dW, cudaStream_t st) {
+  const int32_t chunks = std::max(1, (n + WG_CHUNK - 1) / WG_CHUNK);
+  if (n == 0) {
+    DECO_CUDA_TRY(cudaMemsetAsync(dW, 0, sizeof(float) * (size_t)F * H, st));
+    return DECO_OK;
+  }
+  k_wgrad_part<<<chunks, WG_THREADS, sizeof(float) * WG_TILE * (F + H), st>>>(n, F, H, in, d, part);
+  k_wgrad_sum<<<(F * H + 255) / 256, 256, 0, st>>>(chunks, F * H, part, dW);
+  DECO_CUDA_TRY(cudaGetLastError());
+  return DECO_OK;
+}
+
 int loss_backward(const deco_mpnn* m, const deco_graph* g, const FeatureInfo& fi, const uint8_t* z, Acts& a,
                   float* grad, double* loss_out, cudaStream_t st, double* loss_dev = nullptr) {
   const int32_t n = g->n, H = m->hidden, L = m->layers, G = fi.n_graphs;
@@ -342,6 +386,10 @@ int loss_backward(const deco_mpnn* m, const deco_graph* g, const FeatureInfo& fi
   if ((rc = a.s->alloc(&lp, sizeof(double) * G)) || (rc = a.s->alloc(&lm, sizeof(double) * G)) ||
       (rc = a.s->alloc(&dout, sizeof(float) * n)) || (rc = a.s->alloc(&dH, sizeof(float) * (size_t)n * H)) ||
       (rc = a.s->alloc(&dH2, sizeof(float) * (size_t)n * H)) || (rc = a.s->alloc(&tmp, sizeof(float) * (size_t)n * H)))
+    return rc;
+  float* part = nullptr;   // partial weight-gradient sums, one block of H x H per node chunk
+  if ((rc = a.s->alloc(&part, sizeof(float) * (size_t)std::max(1, (n + WG_CHUNK - 1) / WG_CHUNK) *
+                                  std::max(H * H, F_IN * H))))
     return rc;
   DECO_CUDA_TRY(cudaMemsetAsync(lp, 0, sizeof(double) * G, st));
   DECO_CUDA_TRY(cudaMemsetAsync(lm, 0, sizeof(double) * G, st));
@@ -363,15 +411,17 @@ int loss_backward(const deco_mpnn* m, const deco_graph* g, const FeatureInfo& fi
   if (!grad) return DECO_OK;
   const float* th = m->theta;
   // head: dwo = H_L^T dout, dbo = sum dout, dH_L = dout wo^T
-  k_wgrad<<<H, 32, 0, st>>>(n, H, 1, a.Hs[L], dout, grad + lo.wo);   // H x 1
-  k_bgrad<<<1, 32, 0, st>>>(n, 1, dout, grad + lo.bo);
+  if ((rc = wgrad(n, H, 1, a.Hs[L], dout, part, grad + lo.wo, st)) ||   // H x 1
+      (rc = wgrad(n, 1, 1, nullptr, dout, part, grad + lo.bo, st)))
+    return rc;
   k_outer<<<nb((int64_t)n * H), 256, 0, st>>>(n, H, dout, th + lo.wo, dH);
   DECO_CUDA_TRY(cudaGetLastError());
   for (int l = L; l >= 1; --l) {
     k_relu_mask<<<nb((int64_t)n * H), 256, 0, st>>>((int64_t)n * H, a.pre[l], dH);   // dH -> dpre
-    k_wgrad<<<H, H, 0, st>>>(n, H, H, a.Hs[l - 1], dH, grad + lo.Ws[l - 1]);
-    k_wgrad<<<H, H, 0, st>>>(n, H, H, a.Ms[l - 1], dH, grad + lo.Wn[l - 1]);
-    k_bgrad<<<1, H, 0, st>>>(n, H, dH, grad + lo.b[l - 1]);
+    if ((rc = wgrad(n, H, H, a.Hs[l - 1], dH, part, grad + lo.Ws[l - 1], st)) ||
+        (rc = wgrad(n, H, H, a.Ms[l - 1], dH, part, grad + lo.Wn[l - 1], st)) ||
+        (rc = wgrad(n, 1, H, nullptr, dH, part, grad + lo.b[l - 1], st)))
+      return rc;
     // dH_{l-1} = dpre Ws^T + A (D^-1 (dpre Wn^T))
     k_dense_t<<<(unsigned)((n + 256 / H - 1) / (256 / H)), (256 / H) * H, sizeof(float) * H * H, st>>>(
         n, H, H, dH, th + lo.Wn[l - 1], tmp, 0);
@@ -383,9 +433,10 @@ int loss_backward(const deco_mpnn* m, const deco_graph* g, const FeatureInfo& fi
     std::swap(dH, dH2);
   }
   k_relu_mask<<<nb((int64_t)n * H), 256, 0, st>>>((int64_t)n * H, a.pre[0], dH);
-  k_wgrad<<<F_IN, H, 0, st>>>(n, F_IN, H, a.X, dH, grad + lo.W0);
-  k_bgrad<<<1, H, 0, st>>>(n, H, dH, grad + lo.b0);
   DECO_CUDA_TRY(cudaGetLastError());
+  if ((rc = wgrad(n, F_IN, H, a.X, dH, part, grad + lo.W0, st)) ||
+      (rc = wgrad(n, 1, H, nullptr, dH, part, grad + lo.b0, st)))
+    return rc;
   return DECO_OK;
 }
 
