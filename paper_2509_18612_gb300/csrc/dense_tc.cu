@@ -119,6 +119,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// the same MMA with the A operand (128 rows x 16 K, two BF16 per 32-bit
+// column, K-major) read from tensor memory
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                : "memory");
@@ -138,6 +148,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* out) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) out[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -356,17 +378,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 
 constexpr int PT = 192;          // threads of the phase kernel
 constexpr int PNV = 8;           // update vectors per thread at most
-constexpr int P_MAX_STAGES = 4;
+constexpr int P_MAX_SB = 16;     // B stages (one YT tile each)
+constexpr int P_MAX_SA = 4;      // A stages (the streamed A tiles)
+constexpr int P_RESIDENT = 12;   // A chunks kept in tensor memory (12 x 32 columns + the 128-column accumulator)
 
 struct PhaseArgs {
   CUtensorMap tmA;
   CUtensorMap tmY[2];
   DenseStep p;                   // YT / YTout unused: the phase ping-pongs yt[0] / yt[1]
   __nv_bfloat16* yt[2];
+  const __nv_bfloat16* A;        // the dense A (kpad x kpad), for the chunks kept in tensor memory
   unsigned int* gbar;            // grid barrier counter, zero at launch
+  int32_t resident;              // contraction chunks of A kept in tensor memory (the last ones of the range)
   int32_t steps;
   int32_t w;                     // column tile width (multiple of 32, <= 128)
-  int32_t stages;
+  int32_t sb, sa;                // B and A stage counts
   int32_t ncta;
 };
 
@@ -402,6 +428,9 @@ __device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_
       "r"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
 __device__ __forceinline__ void named_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -425,7 +454,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
 template <bool MOM, bool LAP, int KS>
 __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ PhaseArgs args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[P_MAX_STAGES], empty[P_MAX_STAGES], done, recv_full;
+  __shared__ __align__(8) uint64_t full[P_MAX_SB], empty[P_MAX_SB], emptyA[P_MAX_SA], done, recv_full, out_free;
   __shared__ uint32_t tmem_slot;
   __shared__ int sh_timeout;
   const DenseStep& p = args.p;
@@ -436,20 +465,27 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
   const int W = args.w;
   const int cbase = (int)blockIdx.y * W;
   const int nt = min(W, p.cpad - cbase);   // MMA N of this column tile, a multiple of 32
-  const int S = args.stages;
+  const int SB = args.sb, SA = args.sa;
   const int nk = p.kpad / BK;
   const int kb = (int)((int64_t)nk * r / KS), ke = (int)((int64_t)nk * (r + 1) / KS);
   const int nloc = ke - kb;
   const uint32_t a_bytes = BM * BK * 2;
-  const uint32_t stage_bytes = a_bytes + (uint32_t)W * BK * 2;
+  const uint32_t b_bytes = (uint32_t)W * BK * 2;
+  // shared memory: B ring (SB x b_bytes), A ring (SA x a_bytes), receive area;
+  // the partial-product staging `out` reuses the rings between steps
   const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
   unsigned char* const sbase = smem_raw + (base - saddr(smem_raw));
+  const uint32_t abase = base + (uint32_t)SB * b_bytes;
   constexpr int ROWS = BM / KS;
   constexpr int OCT = ROWS / 8;
   const uint32_t blk_bytes = (uint32_t)W * ROWS * 4;                       // one owner's share of the partial
-  float* const out = reinterpret_cast<float*>(sbase + (size_t)S * stage_bytes);   // [KS][W][ROWS]
-  float* const recv = out + (size_t)KS * W * ROWS;                                 // [KS-1][W][ROWS]
-  const uint32_t tmem_cols = nt <= 32 ? 32u : (nt <= 64 ? 64u : 128u);
+  float* const out = reinterpret_cast<float*>(sbase);                                      // [KS][W][ROWS]
+  float* const recv = reinterpret_cast<float*>(sbase + (size_t)SB * b_bytes + (size_t)SA * a_bytes);   // [KS-1][W][ROWS]
+  // chunks [kr, nloc) keep their A tile in tensor memory for the whole phase:
+  // columns 128 + 32 c (64 BF16 per row, two per column) hold chunk kr + c
+  const int R = min(args.resident, nloc);
+  const int kr = nloc - R;
+  const uint32_t tmem_cols = R > 0 ? 512u : (nt <= 32 ? 32u : (nt <= 64 ? 64u : 128u));
   const int nvec = OCT * nt;
   const int i_base = m0 + r * ROWS;
 
@@ -460,12 +496,14 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < SB; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
+    for (int s = 0; s < SA; ++s) mbar_init(&emptyA[s], 1);
     mbar_init(&done, 1);
     mbar_init(&recv_full, 1);
+    mbar_init(&out_free, 1);   // the update warps are done with `out` (ring memory) for the step
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh_timeout = 0;
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&args.tmA)) : "memory");
@@ -475,21 +513,55 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   bool timed_out = false;
+  if (R > 0 && warp >= 2) {
+    // the resident A tiles: row (TMEM lane) 32 quarter + lane, straight from global memory
+    const int quarter = warp & 3, row = quarter * 32 + lane;
+    const __nv_bfloat16* arow = args.A + (size_t)(m0 + row) * p.kpad;
+    for (int c = 0; c < R; ++c) {
+      uint32_t v[32];
+      const uint4* src = reinterpret_cast<const uint4*>(arow + (size_t)(kb + kr + c) * BK);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint4 q = __ldg(src + k);
+        v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+      }
+      tmem_st32(tmem + ((uint32_t)(quarter * 32) << 16) + 128u + 32u * (uint32_t)c, v);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();   // the resident tiles are in place before any MMA
+  tc_fence_after();
 
   if (tid == 0) {
-    // ---------------- TMA producer
-    int64_t g = 0;   // chunk counter over the whole phase
+    // ---------------- TMA producer.  The chunks of a phase take the B stages
+    // in turn (and the streamed ones the A stages in turn); slot and round
+    // advance by one per chunk, the stage of round u is free once the MMAs of
+    // its round u - 1 have completed (phase (u - 1) & 1 of its empty barrier).
+    int bslot = 0, bround = 0, aslot = 0, around = 0;
+    int pre_slot[P_MAX_SB];
     for (int t = 0; t < args.steps && !timed_out; ++t) {
       const CUtensorMap* tmY = &args.tmY[t & 1];
-      const int pre = min(S, nloc);
-      // A tiles of the first stages of this step: no dependence on the new iterate
-      for (int kc = 0; kc < pre; ++kc) {
-        const int64_t gg = g + kc;
-        const int s = (int)(gg % S);
-        if (gg >= S && !mbar_wait(&empty[s], (uint32_t)(gg / S - 1) & 1u)) { timed_out = true; break; }
-        mbar_expect_tx(&full[s], stage_bytes);
-        tma_load_2d(base + (uint32_t)s * stage_bytes, &args.tmA, (kb + kc) * BK, m0, &full[s]);
-      }
+      // the rings also hold `out` between steps: wait until the update of step t-1 is done with it
+      if (t > 0 && !mbar_wait(&out_free, (uint32_t)(t - 1) & 1u)) { timed_out = true; break; }
+      auto acquire = [&](int kc, int& bs) -> bool {   // the chunk's stages are free, its bytes expected
+        bs = bslot;
+        if (bround > 0 && !mbar_wait(&empty[bslot], (uint32_t)(bround - 1) & 1u)) return false;
+        if (++bslot == SB) { bslot = 0; ++bround; }
+        if (kc < kr) {
+          if (around > 0 && !mbar_wait(&emptyA[aslot], (uint32_t)(around - 1) & 1u)) return false;
+          mbar_expect_tx(&full[bs], a_bytes + b_bytes);
+          tma_load_2d(abase + (uint32_t)aslot * a_bytes, &args.tmA, (kb + kc) * BK, m0, &full[bs]);
+          if (++aslot == SA) { aslot = 0; ++around; }
+        } else {
+          mbar_expect_tx(&full[bs], b_bytes);
+        }
+        return true;
+      };
+      // A tiles of the first streamed chunks: no dependence on the new iterate
+      const int pre = min(min(SB, nloc), min(SA, kr));
+      for (int kc = 0; kc < pre && !timed_out; ++kc)
+        if (!acquire(kc, pre_slot[kc])) timed_out = true;
       if (timed_out) break;
       if (t > 0) {
         // grid barrier: every CTA has written its rows of the iterate of step t
@@ -503,34 +575,37 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         if (!ok) { timed_out = true; break; }
         asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
       }
-      for (int kc = 0; kc < pre; ++kc) {
-        const int s = (int)((g + kc) % S);
-        tma_load_2d(base + (uint32_t)s * stage_bytes + a_bytes, tmY, (kb + kc) * BK, cbase, &full[s]);
+      for (int kc = 0; kc < nloc; ++kc) {
+        int bs = 0;
+        if (kc < pre) bs = pre_slot[kc];
+        else if (!acquire(kc, bs)) { timed_out = true; break; }
+        tma_load_2d(base + (uint32_t)bs * b_bytes, tmY, (kb + kc) * BK, cbase, &full[bs]);
       }
-      for (int kc = pre; kc < nloc; ++kc) {
-        const int64_t gg = g + kc;
-        const int s = (int)(gg % S);
-        if (!mbar_wait(&empty[s], (uint32_t)(gg / S - 1) & 1u)) { timed_out = true; break; }
-        const uint32_t sa = base + (uint32_t)s * stage_bytes;
-        mbar_expect_tx(&full[s], stage_bytes);
-        tma_load_2d(sa, &args.tmA, (kb + kc) * BK, m0, &full[s]);
-        tma_load_2d(sa + a_bytes, tmY, (kb + kc) * BK, cbase, &full[s]);
-      }
-      g += nloc;
     }
   } else if (tid == 32) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer (the same slot / round walk as the producer)
     const uint32_t idesc = idesc_bf16(BM, nt);
-    int64_t g = 0;
+    int bslot = 0, bround = 0, aslot = 0;
     for (int t = 0; t < args.steps && !timed_out; ++t) {
-      for (int kc = 0; kc < nloc; ++kc, ++g) {
-        const int s = (int)(g % S);
-        if (!mbar_wait(&full[s], (uint32_t)(g / S) & 1u)) { timed_out = true; break; }
+      for (int kc = 0; kc < nloc; ++kc) {
+        const int s = bslot;
+        if (!mbar_wait(&full[s], (uint32_t)bround & 1u)) { timed_out = true; break; }
+        if (++bslot == SB) { bslot = 0; ++bround; }
         tc_fence_after();
-        const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+        const uint32_t sb = base + (uint32_t)s * b_bytes;
+        if (kc < kr) {
+          const uint32_t as = abase + (uint32_t)aslot * a_bytes;
 #pragma unroll
-        for (int q = 0; q < BK / 16; ++q)
-          mma_bf16(tmem, desc_sw128(sa + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+          for (int q = 0; q < BK / 16; ++q)
+            mma_bf16(tmem, desc_sw128(as + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+          mma_commit(&emptyA[aslot]);
+          if (++aslot == SA) aslot = 0;
+        } else {
+          const uint32_t at = tmem + 128u + 32u * (uint32_t)(kc - kr);   // K = 16: 8 columns
+#pragma unroll
+          for (int q = 0; q < BK / 16; ++q)
+            mma_bf16_ta(tmem, at + 8u * q, desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+        }
         mma_commit(&empty[s]);
       }
       mma_commit(&done);   // phase t of `done`: the accumulator of step t is complete
@@ -646,8 +721,10 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       if (KS > 1 && et == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // `out` reusable
       asm volatile("fence.proxy.async.global;" ::: "memory");   // new rows -> the next step's TMA reads
       named_sync(1, 128);
-      if (et == 0 && t + 1 < args.steps)
+      if (et == 0 && t + 1 < args.steps) {
+        mbar_arrive_local(&out_free);   // the rings may take the next step's tiles
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(args.gbar) : "memory");
+      }
     }
     if (MOM) {
 #pragma unroll
@@ -809,18 +886,28 @@ int dense_phase_shape(int32_t kpad, int32_t cpad, int ks, int w, DensePhaseShape
   }
   const int rows = BM / ks;
   const size_t out_b = (size_t)ks * w * rows * 4, recv_b = (size_t)(ks - 1) * w * rows * 4;
-  const size_t stage = (size_t)BM * BK * 2 + (size_t)w * BK * 2;
-  const long long room = (long long)optin - 1024 - 512 - (long long)(out_b + recv_b);
-  const int S = room > 0 ? (int)std::min<long long>(P_MAX_STAGES, room / (long long)stage) : 0;
+  const size_t a_st = (size_t)BM * BK * 2, b_st = (size_t)w * BK * 2;
+  const long long room = (long long)optin - 1024 - 512 - (long long)recv_b;
   const int nk = kpad / BK;
-  if (S < 2 || w < 32 || w > 128 || w % 32 || ks > nk || (ks & (ks - 1)) || ks > 8 || (w + 8 * ks - 1) / (8 * ks) > PNV) {
+  if (w < 32 || w > 128 || w % 32 || ks > nk || (ks & (ks - 1)) || ks > 8 || (w + 8 * ks - 1) / (8 * ks) > PNV ||
+      room <= 0) {
+    set_error("dense phase kernel: no shape for w=%d ks=%d", w, ks);
+    return DECO_ERR_UNSUPPORTED;
+  }
+  // the streamed chunks (nk/ks - P_RESIDENT at most) need few A stages; the rest goes to B stages
+  const int streamed = std::max(0, nk / ks - P_RESIDENT);
+  const int SA = std::max(1, std::min(3, streamed));
+  const long long left = room - (long long)SA * (long long)a_st;
+  const int SB = left > 0 ? (int)std::min<long long>(P_MAX_SB, left / (long long)b_st) : 0;
+  if (SB < 2 || (size_t)SB * b_st + (size_t)SA * a_st < out_b) {
     set_error("dense phase kernel: no shape for w=%d ks=%d", w, ks);
     return DECO_ERR_UNSUPPORTED;
   }
   out->w = w;
   out->ks = ks;
-  out->stages = S;
-  out->smem = (size_t)S * stage + out_b + recv_b + 1024;
+  out->stages = SB;
+  out->stages_a = SA;
+  out->smem = (size_t)SB * b_st + (size_t)SA * a_st + recv_b + 1024;
   out->ctas = kpad / BM * ks * ((cpad + w - 1) / w);
   return DECO_OK;
 }
@@ -918,10 +1005,13 @@ int launch_dense_phase(const DenseStep& p, const DenseMaps& maps, __nv_bfloat16*
   args.p = p;
   args.yt[0] = yt[0];
   args.yt[1] = yt[1];
+  args.A = p.A;
+  args.resident = p.A && sh.w <= 128 ? P_RESIDENT : 0;
   args.gbar = gbar;
   args.steps = steps;
   args.w = sh.w;
-  args.stages = sh.stages;
+  args.sb = sh.stages;
+  args.sa = sh.stages_a;
   args.ncta = sh.ctas;
   if ((e = cudaMemsetAsync(gbar, 0, sizeof(unsigned int), st)) != cudaSuccess) return cuda_fail(e, "memset");
   attr[1].id = cudaLaunchAttributeCooperative;

@@ -20,6 +20,7 @@ struct DenseStep {
   int32_t C;            // active columns
   int32_t ks;           // contraction split (cluster size along K)
   int objective;
+  const __nv_bfloat16* A;   // kpad x kpad dense A (read directly by the phase kernel's resident tiles)
   const __nv_bfloat16* YT;  // cpad x kpad, transposed iterate (zero for nodes >= n)
   __nv_bfloat16* YTout;     // cpad x kpad, next iterate (distinct from YT)
   float* VT;                // cpad x kpad momentum (MOM only)
@@ -43,7 +44,8 @@ struct DenseMaps {
 struct DensePhaseShape {
   int w = 0;          // column tile width (multiple of 32, <= 128)
   int ks = 1;         // contraction split (cluster size)
-  int stages = 0;     // TMA stage ring depth
+  int stages = 0;     // B stages (YT tiles)
+  int stages_a = 0;   // A stages (the streamed A tiles)
   size_t smem = 0;    // dynamic shared memory
   int ctas = 0;       // row tiles x ks x column tiles
 };

@@ -325,6 +325,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     p.C = C;
     p.ks = plan.ks;
     p.objective = objective;
+    p.A = g->dense;
     p.VT = momv ? vt : nullptr;
     p.dnet = g->dnet;
     const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
