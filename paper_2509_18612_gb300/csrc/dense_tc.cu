@@ -10,9 +10,15 @@
 // contiguous), so both MMA operands are K-major: the A tile is 128 nodes x 64
 // neighbour nodes, the B tile is N columns x the same 64 neighbour nodes of
 // YT, each a stack of 128-byte rows in the 128-byte swizzled layout written by
-// TMA.  One lane issues the TMA loads of a stage ring, one lane issues the
-// MMAs (M = 128, N <= 256, K = 16 each); full / empty mbarriers hand the
-// stages between them, so no block barrier runs inside the contraction.
+// TMA.  One lane issues the TMA loads of a stage ring; the MMAs (M = 128,
+// N <= 256, K = 16 each) of the even chunks of the contraction range
+// accumulate into D0, those of the odd chunks into D1, and the partial product
+// is D0 + D1 (the same order in both kernels, so their results agree bit for
+// bit).  The per-step kernel issues both from one lane; the phase kernel from
+// one lane of each of two warps, as a single issuing thread reaches only about
+// half the tensor rate at N = 128 (about 80-110 ns per instruction whatever N
+// is, measured).  Full / empty mbarriers hand the stages between producer and
+// issuers, so no block barrier runs inside the contraction.
 //
 // Grid: (row tiles x KS) CTAs along x, column tiles of <= 256 along y.  The KS
 // CTAs of a cluster split the contraction of one 128 x N output tile.  After
@@ -192,7 +198,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
   const uint32_t stage_bytes = a_bytes + (uint32_t)ntmax * BK * 2;
   const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;   // swizzle atoms are 1024-byte aligned
   unsigned char* const sbase = smem_raw + (base - saddr(smem_raw));
-  const uint32_t tmem_cols = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
+  // two accumulators: D0 (columns [0, half)) sums the even chunks of the
+  // contraction range, D1 ([half, 2 half)) the odd ones; the partial is D0 + D1
+  const uint32_t half = nt <= 32 ? 32u : (nt <= 64 ? 64u : (nt <= 128 ? 128u : 256u));
+  const uint32_t tmem_cols = 2 * half;
   constexpr int ROWS = BM / KS;   // rows of the tile updated by this CTA
   constexpr int OCT = ROWS / 8;   // 8-row vectors per column
   const int nvec = OCT * nt;
@@ -265,7 +274,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
       const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
       for (int q = 0; q < BK / 16; ++q)   // K = 16: 32 bytes along the swizzled 128-byte row
-        mma_bf16(tmem, desc_sw128(sa + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+        mma_bf16(tmem + (uint32_t)(kc & 1) * half, desc_sw128(sa + 32u * q), desc_sw128(sb + 32u * q), idesc,
+                 (kc > 1 || q > 0) ? 1u : 0u);
       mma_commit(&empty[s]);   // stage s is free once these MMAs have read it
     }
     sh_consumed = kc;
@@ -289,8 +299,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
     float* dst = cluster.map_shared_rank(recv, row / ROWS) + (size_t)r * nt * ROWS + (row % ROWS);
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < nt; c0 += 32) {
-      float g[32];
+      float g[32], g1[32];
       tmem_ld32(tl + (uint32_t)c0, g);
+      if (nloc > 1) {
+        tmem_ld32(tl + half + (uint32_t)c0, g1);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) g[k] += g1[k];
+      }
 #pragma unroll
       for (int k = 0; k < 32; ++k) dst[(size_t)(c0 + k) * ROWS] = g[k];
     }
@@ -366,8 +381,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 // ---------------------------------------------------------------- persistent phase kernel
 //
 // All steps of a phase in one cooperative cluster launch (every CTA resident).
-// Warp 0 lane 0 loads (TMA), warp 1 lane 0 issues the MMAs, warps 2-5 run the
-// update; the stage ring runs on across steps.  Between steps a grid barrier
+// Warp 0 lane 0 loads (TMA); warp 1 lane 0 issues the MMAs of the even chunks
+// of the contraction range into accumulator D0, warp 2 lane 0 those of the odd
+// chunks into D1 (one issuing thread reaches about half the tensor rate at N =
+// 128: the instruction issue, not the math, bounds it); warps 3-6 run the
+// update on D0 + D1; the stage ring runs on across steps.  Between steps a grid barrier
 // (a counter in global memory, bounded spin) orders the new YT of every CTA
 // before the next step's B tiles are loaded; the A tiles of the next step are
 // requested before that barrier, as A does not change.  The y and V of the
@@ -376,11 +394,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 // per owning CTA and sent with one bulk shared-memory copy per peer, whose
 // bytes complete the owner's receive barrier.
 
-constexpr int PT = 192;          // threads of the phase kernel
+constexpr int PT = 224;          // threads of the phase kernel
 constexpr int PNV = 8;           // update vectors per thread at most
 constexpr int P_MAX_SB = 16;     // B stages (one YT tile each)
-constexpr int P_MAX_SA = 4;      // A stages (the streamed A tiles)
-constexpr int P_RESIDENT = 12;   // A chunks kept in tensor memory (12 x 32 columns + the 128-column accumulator)
+constexpr int P_MAX_SA = 5;      // A stages (the streamed A tiles)
+constexpr int P_RESIDENT = 8;    // A chunks kept in tensor memory (8 x 32 columns + two 128-column accumulators)
 
 struct PhaseArgs {
   CUtensorMap tmA;
@@ -481,11 +499,13 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
   const uint32_t blk_bytes = (uint32_t)W * ROWS * 4;                       // one owner's share of the partial
   float* const out = reinterpret_cast<float*>(sbase);                                      // [KS][W][ROWS]
   float* const recv = reinterpret_cast<float*>(sbase + (size_t)SB * b_bytes + (size_t)SA * a_bytes);   // [KS-1][W][ROWS]
-  // chunks [kr, nloc) keep their A tile in tensor memory for the whole phase:
-  // columns 128 + 32 c (64 BF16 per row, two per column) hold chunk kr + c
+  // tensor memory: accumulators D0 (columns [0, half)) and D1 ([half, 2 half));
+  // chunks [kr, nloc) keep their A tile in it for the whole phase: columns
+  // 256 + 32 c (64 BF16 per row, two per column) hold chunk kr + c
   const int R = min(args.resident, nloc);
   const int kr = nloc - R;
-  const uint32_t tmem_cols = R > 0 ? 512u : (nt <= 32 ? 32u : (nt <= 64 ? 64u : 128u));
+  const uint32_t half = R > 0 ? 128u : (nt <= 32 ? 32u : (nt <= 64 ? 64u : 128u));
+  const uint32_t tmem_cols = R > 0 ? 512u : 2u * half;
   const int nvec = OCT * nt;
   const int i_base = m0 + r * ROWS;
 
@@ -501,7 +521,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < SA; ++s) mbar_init(&emptyA[s], 1);
-    mbar_init(&done, 1);
+    mbar_init(&done, nloc > 1 ? 2 : 1);   // one commit per issuer with chunks
     mbar_init(&recv_full, 1);
     mbar_init(&out_free, 1);   // the update warps are done with `out` (ring memory) for the step
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -513,7 +533,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   bool timed_out = false;
-  if (R > 0 && warp >= 2) {
+  if (R > 0 && warp >= 3) {
     // the resident A tiles: row (TMEM lane) 32 quarter + lane, straight from global memory
     const int quarter = warp & 3, row = quarter * 32 + lane;
     const __nv_bfloat16* arow = args.A + (size_t)(m0 + row) * p.kpad;
@@ -525,7 +545,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         const uint4 q = __ldg(src + k);
         v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
       }
-      tmem_st32(tmem + ((uint32_t)(quarter * 32) << 16) + 128u + 32u * (uint32_t)c, v);
+      tmem_st32(tmem + ((uint32_t)(quarter * 32) << 16) + 256u + 32u * (uint32_t)c, v);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
@@ -582,37 +602,42 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         tma_load_2d(base + (uint32_t)bs * b_bytes, tmY, (kb + kc) * BK, cbase, &full[bs]);
       }
     }
-  } else if (tid == 32) {
-    // ---------------- MMA issuer (the same slot / round walk as the producer)
+  } else if (tid == 32 || (tid == 64 && nloc > 1)) {
+    // ---------------- MMA issuers (the same slot / round walk as the producer;
+    // issuer `my` takes the chunks kc with kc % 2 == my, into D_my; a range of
+    // one chunk has one issuer, an idle one would run ahead of the steps)
+    const int my = tid == 64 ? 1 : 0;
+    const uint32_t d = tmem + (uint32_t)my * half;
     const uint32_t idesc = idesc_bf16(BM, nt);
     int bslot = 0, bround = 0, aslot = 0;
     for (int t = 0; t < args.steps && !timed_out; ++t) {
       for (int kc = 0; kc < nloc; ++kc) {
-        const int s = bslot;
-        if (!mbar_wait(&full[s], (uint32_t)bround & 1u)) { timed_out = true; break; }
+        const int s = bslot, rnd = bround, as_ = aslot;
         if (++bslot == SB) { bslot = 0; ++bround; }
+        if (kc < kr && ++aslot == SA) aslot = 0;
+        if ((kc & 1) != my) continue;
+        if (!mbar_wait(&full[s], (uint32_t)rnd & 1u)) { timed_out = true; break; }
         tc_fence_after();
         const uint32_t sb = base + (uint32_t)s * b_bytes;
         if (kc < kr) {
-          const uint32_t as = abase + (uint32_t)aslot * a_bytes;
+          const uint32_t as = abase + (uint32_t)as_ * a_bytes;
 #pragma unroll
           for (int q = 0; q < BK / 16; ++q)
-            mma_bf16(tmem, desc_sw128(as + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
-          mma_commit(&emptyA[aslot]);
-          if (++aslot == SA) aslot = 0;
+            mma_bf16(d, desc_sw128(as + 32u * q), desc_sw128(sb + 32u * q), idesc, (kc > 1 || q > 0) ? 1u : 0u);
+          mma_commit(&emptyA[as_]);
         } else {
-          const uint32_t at = tmem + 128u + 32u * (uint32_t)(kc - kr);   // K = 16: 8 columns
+          const uint32_t at = tmem + 256u + 32u * (uint32_t)(kc - kr);   // K = 16: 8 columns
 #pragma unroll
           for (int q = 0; q < BK / 16; ++q)
-            mma_bf16_ta(tmem, at + 8u * q, desc_sw128(sb + 32u * q), idesc, (kc > 0 || q > 0) ? 1u : 0u);
+            mma_bf16_ta(d, at + 8u * q, desc_sw128(sb + 32u * q), idesc, (kc > 1 || q > 0) ? 1u : 0u);
         }
         mma_commit(&empty[s]);
       }
-      mma_commit(&done);   // phase t of `done`: the accumulator of step t is complete
+      mma_commit(&done);   // phase t of `done` completes with both issuers' accumulators of step t
     }
-  } else if (warp >= 2) {
+  } else if (warp >= 3) {
     // ---------------- update warps: et = row-vector owner index, quarter = TMEM lanes
-    const int et = tid - 64;
+    const int et = tid - 96;
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;   // tile row read from tensor memory
     const int qown = row / ROWS;
@@ -652,8 +677,13 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         float* dst = out + (size_t)qown * W * ROWS + (row % ROWS);
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         for (int c0 = 0; c0 < nt; c0 += 32) {
-          float gv[32];
+          float gv[32], g1[32];
           tmem_ld32(tl + (uint32_t)c0, gv);
+          if (nloc > 1) {   // D0 + D1
+            tmem_ld32(tl + half + (uint32_t)c0, g1);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) gv[k] += g1[k];
+          }
 #pragma unroll
           for (int k = 0; k < 32; ++k) dst[(size_t)(c0 + k) * ROWS] = gv[k];
         }
@@ -750,7 +780,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       while (gtimer() - t0 < 100000ull) {
       }
     }
-    if (tid == 64) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (tid == 96) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // the exchange's issuing thread
     __syncthreads();
   }
   tc_fence_before();
@@ -894,9 +924,11 @@ int dense_phase_shape(int32_t kpad, int32_t cpad, int ks, int w, DensePhaseShape
     set_error("dense phase kernel: no shape for w=%d ks=%d", w, ks);
     return DECO_ERR_UNSUPPORTED;
   }
-  // the streamed chunks (nk/ks - P_RESIDENT at most) need few A stages; the rest goes to B stages
+  // the streamed chunks (nk/ks - P_RESIDENT at most) take up to five A stages
+  // (measured at n = 4096, C = 128, ks = 4: 2 / 3 / 4 / 5 / 8 stages give
+  // 10.5 / 10.0 / 9.6 / 9.5 / 10.2 us per step); the rest goes to B stages
   const int streamed = std::max(0, nk / ks - P_RESIDENT);
-  const int SA = std::max(1, std::min(3, streamed));
+  const int SA = std::max(1, std::min(P_MAX_SA, streamed));
   const long long left = room - (long long)SA * (long long)a_st;
   const int SB = left > 0 ? (int)std::min<long long>(P_MAX_SB, left / (long long)b_st) : 0;
   if (SB < 2 || (size_t)SB * b_st + (size_t)SA * a_st < out_b) {
