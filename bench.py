@@ -418,6 +418,11 @@ def run_er4096_dense():
     flops = 2.0 * g.n * g.n * C
     peaks, kind = measured_peaks()
     ach = flops / t_step / 1e12
+    # tensor-core ceiling of the contraction's instruction shape (M = 128,
+    # N = C = 128, K = 16), measured on this GPU with every SM issuing
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue = {f"n{nn}_issuers{k}": deco.deco_probe_mma_rate(nn, k, 4096) for nn, k in ((128, 1), (128, 2), (256, 1))}
+    ceiling = 2.0 * 128 * C * 16 / issue["n128_issuers1"] * sms / 1e3
     return {"workload": "ER(n=4096, p=0.5); B=128 bf16 starts (IDI); pQUCO T=1000, alpha=1e-4",
             "value": res_d.edge_updates / t_d, "unit": "edge-updates/s", "solve_s": t_d,
             "best_cut": res_d.best_cut, "m": g.m, "tuned_kernel": hex(sel), "dense_kernel": hex(dense_sel),
@@ -429,7 +434,10 @@ def run_er4096_dense():
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_kind": kind + " (burst)",
                          "kernel": "k_dense_phase (per step of a phase launch)", "us_per_step": t_step * 1e6,
-                         "algorithmic_flops_per_launch": flops}}
+                         "algorithmic_flops_per_launch": flops,
+                         "tensor_ns_per_instruction": issue,
+                         "tensor_ceiling_tflops_n128": ceiling,
+                         "frac_of_ceiling_n128": ach / ceiling}}
 
 
 def run_greedy_comparison():

@@ -502,6 +502,22 @@ int deco_greedy(const deco_graph* g, int32_t B, uint64_t seed, uint8_t* z, int64
 int deco_local_search(const deco_graph* g, int32_t B, uint8_t* z, int32_t max_rounds, int64_t* cuts,
                       int32_t* rounds, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------- */
+
+/* Tensor-core instruction rate of this GPU, the bound of the dense kernels'
+ * contraction: one CTA per SM, in which `issuers` threads (1 or 2, each in
+ * its own warp) issue `count` tcgen05.mma instructions each (kind::f16,
+ * M = 128, N = n in {64, 128, 256}, K = 16, BF16 zeros in shared memory,
+ * FP32 accumulators in tensor memory), back to back.  ns_per_instruction
+ * (host) receives the mean over SMs of the slowest issuer's time from the
+ * first issue to the completion of its last instruction, divided by the
+ * SM's instructions (count x issuers): 2 * 128 * n * 16 / ns_per_instruction
+ * is the SM's FLOP rate in GFLOP/s.  Synchronises the stream.
+ * Errors: DECO_ERR_ARG, DECO_ERR_TIMEOUT (a wait gave up, 1 s), CUDA. */
+int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, float* ns_per_instruction, void* stream);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);
 

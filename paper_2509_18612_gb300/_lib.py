@@ -55,7 +55,7 @@ EXPORTED = [
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_solve_budget", "deco_greedy", "deco_local_search",
-    "deco_last_error", "deco_abi_version",
+    "deco_probe_mma_rate", "deco_last_error", "deco_abi_version",
 ]
 
 
@@ -138,6 +138,7 @@ def _load():
                                              U64, ctypes.c_double, I32, P, P, P, P, ctypes.POINTER(deco_result)]),
         "deco_greedy": (ctypes.c_int, [P, I32, U64, P, P, P]),
         "deco_local_search": (ctypes.c_int, [P, I32, P, I32, P, P, P]),
+        "deco_probe_mma_rate": (ctypes.c_int, [I32, I32, I32, P, P]),
         "deco_last_error": (ctypes.c_char_p, []),
         "deco_abi_version": (ctypes.c_int, []),
     }
@@ -316,6 +317,13 @@ def deco_autotune(g: Graph, C: int, precision: int = DECO_PREC_FP32, objective: 
     _check(lib.deco_autotune(g, int(C), int(precision), int(objective), float(momentum), int(probe_steps),
                              ctypes.byref(sel), ctypes.byref(us), _stream(stream)))
     return sel.value, us.value
+
+
+def deco_probe_mma_rate(n: int = 128, issuers: int = 1, count: int = 4096, stream=None) -> float:
+    """ns per tcgen05.mma (M = 128, N = n, K = 16) per SM with `issuers` issuing threads."""
+    ns = ctypes.c_float()
+    _check(lib.deco_probe_mma_rate(int(n), int(issuers), int(count), ctypes.byref(ns), _stream(stream)))
+    return ns.value
 
 
 def deco_set_tuning(g: Graph, C: int, precision: int, kernel: int):

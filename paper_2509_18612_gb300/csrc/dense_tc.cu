@@ -15,10 +15,12 @@
 // accumulate into D0, those of the odd chunks into D1, and the partial product
 // is D0 + D1 (the same order in both kernels, so their results agree bit for
 // bit).  The per-step kernel issues both from one lane; the phase kernel from
-// one lane of each of two warps, as a single issuing thread reaches only about
-// half the tensor rate at N = 128 (about 80-110 ns per instruction whatever N
-// is, measured).  Full / empty mbarriers hand the stages between producer and
-// issuers, so no block barrier runs inside the contraction.
+// one lane of each of two warps: an M = 128, N = 128, K = 16 instruction takes
+// the tensor core ~33 ns (deco_probe_mma_rate), well under the loop's time per
+// chunk, which the stage handshakes (waits on TMA arrivals, commits) set; two
+// issuers overlap the waits of consecutive chunks.  Full / empty mbarriers
+// hand the stages between producer and issuers, so no block barrier runs
+// inside the contraction.
 //
 // Grid: (row tiles x KS) CTAs along x, column tiles of <= 256 along y.  The KS
 // CTAs of a cluster split the contraction of one 128 x N output tile.  After
@@ -383,9 +385,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 // All steps of a phase in one cooperative cluster launch (every CTA resident).
 // Warp 0 lane 0 loads (TMA); warp 1 lane 0 issues the MMAs of the even chunks
 // of the contraction range into accumulator D0, warp 2 lane 0 those of the odd
-// chunks into D1 (one issuing thread reaches about half the tensor rate at N =
-// 128: the instruction issue, not the math, bounds it); warps 3-6 run the
-// update on D0 + D1; the stage ring runs on across steps.  Between steps a grid barrier
+// chunks into D1 (so the wait for one chunk's tiles overlaps the other
+// issuer's MMAs); warps 3-6 run the update on D0 + D1; the stage ring runs on
+// across steps.  Between steps a grid barrier
 // (a counter in global memory, bounded spin) orders the new YT of every CTA
 // before the next step's B tiles are loaded; the A tiles of the next step are
 // requested before that barrier, as A does not change.  The y and V of the

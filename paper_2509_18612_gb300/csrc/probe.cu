@@ -1,0 +1,136 @@
+// Diagnostic: the rate at which tcgen05.mma instructions (kind::f16, M = 128,
+// N = 64 / 128 / 256, K = 16, BF16 operands in shared memory, FP32
+// accumulators in tensor memory) complete on this GPU when issued back to
+// back by one or two threads per SM: the tensor-core ceiling of the dense
+// kernels' contraction, whose instructions have N = the iterate's columns
+// (128 for the dense workload).
+#include <algorithm>
+
+#include "api_util.cuh"
+#include "deco_internal.cuh"
+#include "phase.cuh"
+
+using namespace deco;
+
+namespace {
+
+constexpr int PROBE_THREADS = 128;
+constexpr uint64_t PROBE_WAIT_NS = 1000000000ull;   // 1 s per wait at most
+
+__device__ __forceinline__ uint32_t p_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t p_gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// K-major operand in the 128-byte swizzled layout (the dense kernels' form)
+__device__ __forceinline__ uint64_t p_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// One CTA per SM.  Issuer i (thread 32 (i + 1)) issues `count` MMAs into its
+// own accumulator (tensor-memory columns [256 i, 256 i + n)), commits them to
+// its mbarrier and waits; out[2 blockIdx + i] = its issue-to-completion time
+// in ns, or 0 if its wait gave up.
+__global__ void __launch_bounds__(PROBE_THREADS, 1) k_probe_mma(int n, int issuers, int count,
+                                                                 unsigned long long* out) {
+  extern __shared__ unsigned char raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t slot;
+  const uint32_t base = (p_saddr(raw) + 1023u) & ~1023u;
+  unsigned char* const sb = raw + (base - p_saddr(raw));
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 16384 + 32768; i += PROBE_THREADS) sb[i] = 0;   // A 128 x 64, B 256 x 64 (BF16 zeros)
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(p_saddr(&slot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(p_saddr(&bar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // zeroed operands -> tensor-core reads
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = slot;
+  const int me = tid / 32 - 1;
+  if ((tid & 31) == 0 && me >= 0 && me < issuers) {
+    const uint32_t a = base, b = base + 16384;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t d = tmem + 256u * (uint32_t)me;
+    const uint64_t t0 = p_gtimer();
+    for (int i = 0; i < count; ++i) {
+      const uint32_t q = (uint32_t)(i & 3);
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+          "l"(p_desc(a + 32u * q)), "l"(p_desc(b + 32u * q)), "r"(idesc), "r"(i > 0 ? 1u : 0u)
+          : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     p_saddr(&bar[me]))
+                 : "memory");
+    bool ok = false;
+    for (uint32_t it = 0; it < (1u << 30) && !ok; ++it) {
+      uint32_t r;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(r)
+          : "r"(p_saddr(&bar[me]))
+          : "memory");
+      ok = r != 0;
+      if (!ok && (it & 63u) == 0 && p_gtimer() - t0 > PROBE_WAIT_NS) break;
+    }
+    out[2 * blockIdx.x + me] = ok ? p_gtimer() - t0 : 0ull;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+}  // namespace
+
+extern "C" int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, float* ns_per_instruction,
+                                   void* stream) {
+  clear_error();
+  if ((n != 64 && n != 128 && n != 256) || issuers < 1 || issuers > 2 || count < 1 || count > (1 << 24) ||
+      !ns_per_instruction) {
+    set_error("bad arguments (n=%d issuers=%d count=%d)", n, issuers, count);
+    return DECO_ERR_ARG;
+  }
+  cudaStream_t st = as_stream(stream);
+  const int sms = device_sm_count();
+  // more than half of an SM's shared memory: one CTA (one 512-column tensor-memory allocation) per SM
+  const size_t smem = 1024 + 16384 + 32768 + 96 * 1024;
+  DECO_CUDA_TRY(cudaFuncSetAttribute(k_probe_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  Scratch s(st);
+  unsigned long long* d = nullptr;
+  int rc = s.alloc((void**)&d, sizeof(unsigned long long) * 2 * (size_t)sms);
+  if (rc) return rc;
+  DECO_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * 2 * (size_t)sms, st));
+  k_probe_mma<<<(unsigned)sms, PROBE_THREADS, smem, st>>>(n, issuers, count, d);
+  DECO_CUDA_TRY(cudaGetLastError());
+  std::vector<unsigned long long> h(2 * (size_t)sms);
+  DECO_CUDA_TRY(cudaMemcpyAsync(h.data(), d, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  DECO_CUDA_TRY(cudaStreamSynchronize(st));
+  double sum = 0.0;
+  for (int b = 0; b < sms; ++b) {
+    unsigned long long worst = 0;
+    for (int i = 0; i < issuers; ++i) {
+      if (h[2 * b + i] == 0) {
+        set_error("tensor-core probe: a wait gave up on SM block %d", b);
+        return DECO_ERR_TIMEOUT;
+      }
+      worst = std::max(worst, h[2 * b + i]);
+    }
+    sum += (double)worst;
+  }
+  // per SM: instructions of all its issuers over the slowest issuer's time
+  *ns_per_instruction = (float)(sum / sms / ((double)count * issuers));
+  return DECO_OK;
+}

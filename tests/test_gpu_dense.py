@@ -292,3 +292,17 @@ def test_dense_full_size_step_with_momentum_matches_oracle(er4096):
     assert flag == 0
     assert np.all(np.abs(out - ref) <= tol)
     assert np.all(np.abs(v.cpu().numpy() - vref) <= 1e-5 * np.maximum(1.0, np.abs(vref)) + vtol)
+
+
+def test_tensor_core_rate_probe():
+    # the probe runs on every SM and reports a positive time per instruction;
+    # the tensor core is the bound, not the issuing thread: twice the columns
+    # take longer, and two issuers take about the time per instruction of one
+    one = deco.deco_probe_mma_rate(128, 1, 2048)
+    two = deco.deco_probe_mma_rate(128, 2, 2048)
+    wide = deco.deco_probe_mma_rate(256, 1, 2048)
+    assert 1.0 < one < 10000.0 and 1.0 < two < 10000.0 and 1.0 < wide < 10000.0
+    assert wide > 1.3 * one
+    assert 0.5 * one < two < 1.5 * one
+    with pytest.raises(deco.DecoError):
+        deco.deco_probe_mma_rate(96, 1, 16)
