@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define DECO_ABI_VERSION 1
+#define DECO_ABI_VERSION 2
 
 typedef enum deco_status {
   DECO_OK = 0,
@@ -299,7 +299,26 @@ typedef struct deco_params {
                                  phase's rounded vectors before their cuts are
                                  evaluated; 0 = off (the paper's method).  Not
                                  available in deco_solve_batch. */
+  int32_t phase_init;         /* deco_solve, phases after the first:
+                                 DECO_PHASE_INIT_BEST (0, Sec. 4.2): Gaussian
+                                 starts around 2 z* - 1 of the previous phase's
+                                 best vector; DECO_PHASE_INIT_FRESH (1): a fresh
+                                 start of the first phase's kind (init), its
+                                 random draws with the phase index in the
+                                 counter (not with DECO_INIT_EXPLICIT).  Batches:
+                                 0 only. */
+  int32_t eval_every;         /* deco_solve: 0 = off; E > 0 also rounds every
+                                 start after steps E, 2E, ... < T_k of every
+                                 phase (best-so-far tracking for time-to-target):
+                                 these cuts count toward best_cut / best_init /
+                                 best_phase / the assignment (ties: the earlier
+                                 evaluation); phase_cuts and the next phase's
+                                 centre stay the final roundings'.  Batches: 0
+                                 only. */
 } deco_params;
+
+#define DECO_PHASE_INIT_BEST 0
+#define DECO_PHASE_INIT_FRESH 1
 
 int deco_init_block(const deco_graph* g, int32_t B, int32_t lift, int32_t ld,
                     const deco_params* p, uint64_t seed, int32_t phase,

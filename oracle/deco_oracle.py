@@ -409,6 +409,8 @@ class Params:
     uniform_half_width: float = 1.0
     mean: Optional[np.ndarray] = None   # for init == "mean" (e.g. a learned proposal)
     local_search: int = 0     # rounds of 1-flip local search on every phase's rounded vectors (0: off)
+    phase_init: str = "best"  # later phases: "best" (around 2 z* - 1, Sec. 4.2) | "fresh" (like phase 0)
+    eval_every: int = 0       # > 0: also round after steps E, 2E, ... < T_k (best-so-far tracking)
 
 
 @dataclass
@@ -422,29 +424,33 @@ class SolveResult:
     final_Y: Optional[np.ndarray] = None
 
 
-def initial_block(g, B: int, lift: int, params: Params, seed: int, x0=None) -> np.ndarray:
-    """Starting block of the first phase (n x B*lift, centred coordinates)."""
+def initial_block(g, B: int, lift: int, params: Params, seed: int, x0=None, phase: int = 0) -> np.ndarray:
+    """Starting block of the first phase (n x B*lift, centred coordinates);
+    with phase k > 0 the same kind of start with every random draw taken with
+    phase index k in its counter (fresh later phases)."""
     n = g.n
     C = B * lift
+    if params.init == "explicit" and phase > 0:
+        raise ValueError("fresh later phases need a drawn initialisation")
     if params.init == "explicit":
         X0 = np.asarray(x0, dtype=np.float64)
         if X0.shape != (n, C):
             raise ValueError("explicit start must be n x (B*lift)")
         return 2.0 * X0 - 1.0 if params.objective == OBJ_MULTILINEAR01 else X0.copy()
     if params.init == "uniform":
-        return uniform_block(n, C, seed, 0, params.uniform_half_width)
+        return uniform_block(n, C, seed, phase, params.uniform_half_width)
     if params.init == "idi":
-        return gaussian_block(idi_mean(g, seed, 0, params.beta), C, seed, 0, params.eta, params.scale)
+        return gaussian_block(idi_mean(g, seed, phase, params.beta), C, seed, phase, params.eta, params.scale)
     if params.init == "dui":
-        return gaussian_block(dui_mean(g, seed, 0), C, seed, 0, params.eta, params.scale)
+        return gaussian_block(dui_mean(g, seed, phase), C, seed, phase, params.eta, params.scale)
     if params.init == "mean":
-        return gaussian_block(params.mean, C, seed, 0, params.eta, params.scale)
+        return gaussian_block(params.mean, C, seed, phase, params.eta, params.scale)
     if params.init == "idi_half_uniform":
         # Reading: inits [0, B/2) are IDI-centred Gaussians, inits [B/2, B) are
         # uniform draws scaled like the Gaussian ones.
-        Y = uniform_block(n, C, seed, 0, params.scale)
+        Y = uniform_block(n, C, seed, phase, params.scale)
         half = (B // 2) * lift
-        Y[:, :half] = gaussian_block(idi_mean(g, seed, 0, params.beta), half, seed, 0,
+        Y[:, :half] = gaussian_block(idi_mean(g, seed, phase, params.beta), half, seed, phase,
                                      params.eta, params.scale)
         return Y
     raise ValueError(params.init)
@@ -473,29 +479,47 @@ def solve(g, B: int, phases: Sequence[Phase], params: Params, seed: int, x0=None
     After each phase the block is binarised (Eq. 5 / 11), every init's cut is
     evaluated (Eq. 1) and the best is kept; the global best is the first
     strictly larger cut over phases (ties keep the earlier phase).
+    params.phase_init == "fresh": later phases start like phase 0, with phase
+    index k in the random draws.  params.eval_every = E > 0: the block is also
+    binarised after steps E, 2E, ... < T_k of every phase; those cuts compete
+    for the global best (ties keep the earlier rounding), while phase_cuts and
+    the next phase's centre stay the final roundings'.
     """
-    best_cut, best_init, best_phase, assignment = None, -1, -1, None
-    phase_cuts, phase_best = [], []
-    prev_best_z = None
-    Y = None
-    for k, ph in enumerate(phases):
-        if k == 0:
-            Y = initial_block(g, B, ph.lift, params, seed, x0)
-        else:
-            h = 2.0 * prev_best_z.astype(np.float64) - 1.0
-            Y = gaussian_block(h, B * ph.lift, seed, k, params.eta, params.scale)
-        Y = run_phase(g, Y, ph, params.objective)
-        Z = binarize(Y, ph.lift)
+    best = {"cut": None, "init": -1, "phase": -1, "z": None}
+
+    def rounding(Yk, k, lift):
+        Z = binarize(Yk, lift)
         if params.local_search > 0:
             Z, _ = local_search(g, Z, params.local_search)
         cuts = cut_values(g, Z)
         b = best_of(cuts)
+        if best["cut"] is None or int(cuts[b]) > best["cut"]:
+            best.update(cut=int(cuts[b]), init=b, phase=k, z=Z[:, b].copy())
+        return Z, cuts, b
+
+    phase_cuts, phase_best = [], []
+    prev_best_z = None
+    Y = None
+    for k, ph in enumerate(phases):
+        if k == 0 or params.phase_init == "fresh":
+            Y = initial_block(g, B, ph.lift, params, seed, x0, phase=k)
+        else:
+            h = 2.0 * prev_best_z.astype(np.float64) - 1.0
+            Y = gaussian_block(h, B * ph.lift, seed, k, params.eta, params.scale)
+        if params.eval_every > 0:
+            A, d = adjacency(g), net_degree(g)
+            V = np.zeros_like(Y)
+            for t in range(ph.steps):
+                Y, V = pga_step(g, Y, ph.alpha, params.objective, V, ph.momentum, A=A, d=d)
+                if t + 1 < ph.steps and (t + 1) % params.eval_every == 0:
+                    rounding(Y, k, ph.lift)
+        else:
+            Y = run_phase(g, Y, ph, params.objective)
+        Z, cuts, b = rounding(Y, k, ph.lift)
         phase_cuts.append(cuts)
         phase_best.append(b)
         prev_best_z = Z[:, b].copy()
-        if best_cut is None or int(cuts[b]) > best_cut:
-            best_cut, best_init, best_phase = int(cuts[b]), b, k
-            assignment = Z[:, b].copy()
+    best_cut, best_init, best_phase, assignment = best["cut"], best["init"], best["phase"], best["z"]
     return SolveResult(best_cut=best_cut, best_init=best_init, best_phase=best_phase,
                        assignment=assignment, phase_cuts=phase_cuts, phase_best=phase_best,
                        final_Y=Y if keep_final else None)

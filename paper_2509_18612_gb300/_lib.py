@@ -39,6 +39,8 @@ DECO_INIT_DUI = 2
 DECO_INIT_IDI_HALF_UNIFORM = 3
 DECO_INIT_EXPLICIT = 4
 DECO_INIT_MEAN = 5
+DECO_PHASE_INIT_BEST = 0
+DECO_PHASE_INIT_FRESH = 1
 DECO_GRAPH_SKIP_SYMMETRY_CHECK = 0x1
 DECO_KERNEL_AUTO = 0
 DECO_KERNEL_GLOBAL = 1
@@ -77,7 +79,7 @@ class deco_params(ctypes.Structure):
                 ("init", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
                 ("eta", ctypes.c_float), ("scale", ctypes.c_float), ("beta", ctypes.c_float),
                 ("uniform_half_width", ctypes.c_float), ("kernel", ctypes.c_int32),
-                ("local_search", ctypes.c_int32)]
+                ("local_search", ctypes.c_int32), ("phase_init", ctypes.c_int32), ("eval_every", ctypes.c_int32)]
 
 
 class deco_phase(ctypes.Structure):
@@ -338,9 +340,9 @@ def deco_round_cut(g: Graph, B: int, lift: int, ld: int, precision: int, y, zbit
 
 def params(objective=DECO_OBJ_MULTILINEAR01, precision=DECO_PREC_FP32, init=DECO_INIT_UNIFORM,
            polish_steps=0, eta=0.8, scale=1e-4, beta=0.2, uniform_half_width=1.0,
-           kernel=DECO_KERNEL_AUTO, local_search=0) -> deco_params:
+           kernel=DECO_KERNEL_AUTO, local_search=0, phase_init=0, eval_every=0) -> deco_params:
     return deco_params(objective, precision, init, polish_steps, eta, scale, beta, uniform_half_width,
-                       kernel, local_search)
+                       kernel, local_search, phase_init, eval_every)
 
 
 def deco_init_block(g: Graph, B: int, lift: int, ld: int, p: deco_params, seed: int, phase: int, y,

@@ -258,6 +258,10 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
   if (rc || (rc = check_obj(p->objective))) return rc;
   if (!valid_selector(p->kernel)) { set_error("bad kernel selector 0x%x", p->kernel); return DECO_ERR_ARG; }
   if (p->local_search != 0) { set_error("the local search is not available in batched solves"); return DECO_ERR_UNSUPPORTED; }
+  if (p->phase_init != DECO_PHASE_INIT_BEST || p->eval_every != 0) {
+    set_error("fresh later phases and intermediate roundings are not available in batched solves");
+    return DECO_ERR_UNSUPPORTED;
+  }
   const int32_t P = pop->candidates;
   if (B < 1 || P < 1 || B % P || pop->rounds < 1 || pop->t_lo < 0 || pop->t_hi < pop->t_lo ||
       !(pop->e_hi >= pop->e_lo) || pop->n_lifts < 1 || pop->n_lifts > 8) {

@@ -126,11 +126,13 @@ __global__ void k_argmax(int32_t B, const int64_t* cuts, int32_t* best) {
   if (threadIdx.x == 0) *best = si[0];
 }
 
-// Record update: the phase's best, and the global best if strictly larger.
-__global__ void k_record(int32_t phase, const int64_t* cuts, const int32_t* best_idx, BestRecord* rec) {
+// Record update: the evaluation's best becomes the global best if it is the
+// first evaluation of the solve or strictly larger.
+__global__ void k_record(int32_t phase, int32_t first, const int64_t* cuts, const int32_t* best_idx,
+                         BestRecord* rec) {
   const int32_t b = *best_idx;
   const long long c = cuts[b];
-  if (phase == 0 || c > rec->cut) {
+  if (first || c > rec->cut) {
     rec->cut = c;
     rec->init = b;
     rec->phase = phase;
@@ -146,7 +148,7 @@ __global__ void k_extract(int32_t n, int32_t W, const uint32_t* zbits, const int
   if (v >= n) return;
   const int32_t b = *best_idx;
   const uint8_t z = (uint8_t)((zbits[(size_t)v * W + (b >> 5)] >> (b & 31)) & 1u);
-  phase_best_z[v] = z;
+  if (phase_best_z) phase_best_z[v] = z;
   if (rec->improved && best_z) best_z[v] = z;
 }
 
@@ -202,12 +204,12 @@ int launch_argmax(int32_t B, const int64_t* cuts, int32_t* best, cudaStream_t st
   return DECO_OK;
 }
 
-int launch_phase_finish(const deco_graph* g, int32_t B, int32_t phase, const int64_t* cuts,
+int launch_phase_finish(const deco_graph* g, int32_t B, int32_t phase, bool first, const int64_t* cuts,
                         const uint32_t* zbits, int32_t* best_idx, BestRecord* rec,
                         uint8_t* phase_best_z, uint8_t* best_z, cudaStream_t st) {
   int rc = launch_argmax(B, cuts, best_idx, st);
   if (rc) return rc;
-  k_record<<<1, 1, 0, st>>>(phase, cuts, best_idx, rec);
+  k_record<<<1, 1, 0, st>>>(phase, first ? 1 : 0, cuts, best_idx, rec);
   DECO_CUDA_TRY(cudaGetLastError());
   const int32_t W = (B + 31) / 32;
   k_extract<<<(g->n + 255) / 256, 256, 0, st>>>(g->n, W, zbits, best_idx, rec, phase_best_z, best_z);

@@ -162,7 +162,10 @@ struct BestRecord {
   int32_t improved;   // last phase improved the record
   int32_t pad;
 };
-int launch_phase_finish(const deco_graph* g, int32_t B, int32_t phase, const int64_t* cuts,
+// argmax of `cuts` into best_idx; the global record (first evaluation of a
+// solve, or a strictly larger cut) and its vector best_z; the evaluation's
+// best vector into phase_best_z (if not NULL)
+int launch_phase_finish(const deco_graph* g, int32_t B, int32_t phase, bool first, const int64_t* cuts,
                         const uint32_t* zbits, int32_t* best_idx, BestRecord* rec,
                         uint8_t* phase_best_z, uint8_t* best_z, cudaStream_t st);
 

@@ -1,11 +1,12 @@
 // deco_solve: the whole pDECO schedule (Alg. 3) on the device.
 //
 // Per phase k: starting block (phase 0: the requested initialisation; later
-// phases: Gaussian around 2 z* - 1 of the previous phase's best, Sec. 4.2),
-// T_k projected gradient steps (phase runner: persistent on-chip kernel or
-// per-step global kernel), rounding (Eq. 5 / 11), integer cuts (Eq. 1),
-// argmax and the global best record -- all stream-ordered, with one host
-// synchronisation at the end.
+// phases: Gaussian around 2 z* - 1 of the previous phase's best, Sec. 4.2, or
+// a fresh start of the first phase's kind), T_k projected gradient steps
+// (phase runner: persistent on-chip, per-step global or dense kernel; run in
+// segments of eval_every steps when intermediate roundings are asked for),
+// rounding (Eq. 5 / 11), integer cuts (Eq. 1), argmax and the global best
+// record -- all stream-ordered, with one host synchronisation at the end.
 #include <algorithm>
 #include <memory>
 #include <vector>
@@ -49,6 +50,15 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
   if ((rc = check_prec(p->precision)) || (rc = check_obj(p->objective))) return rc;
   if (!valid_selector(p->kernel)) { set_error("bad kernel selector 0x%x", p->kernel); return DECO_ERR_ARG; }
   if (p->local_search < 0) { set_error("local_search must be >= 0"); return DECO_ERR_ARG; }
+  if (p->phase_init != DECO_PHASE_INIT_BEST && p->phase_init != DECO_PHASE_INIT_FRESH) {
+    set_error("bad phase_init %d", p->phase_init);
+    return DECO_ERR_ARG;
+  }
+  if (p->phase_init == DECO_PHASE_INIT_FRESH && p->init == DECO_INIT_EXPLICIT) {
+    set_error("fresh later phases need a drawn initialisation, not an explicit block");
+    return DECO_ERR_ARG;
+  }
+  if (p->eval_every < 0) { set_error("eval_every must be >= 0"); return DECO_ERR_ARG; }
   int32_t max_lift = 1;
   bool any_mom = false;
   for (int k = 0; k < n_phases; ++k) {
@@ -97,8 +107,8 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
     DECO_CUDA_TRY(cudaMemsetAsync(ybuf[1], 0, ybytes, st));
     if (any_mom && (rc = s.alloc(&vbuf, block_elems * sizeof(float)))) return rc;
     if ((rc = s.alloc(&zbits, sizeof(uint32_t) * (size_t)n * W))) return rc;
-    if ((rc = s.alloc(&cuts, sizeof(int64_t) * (size_t)B * n_phases))) return rc;
-    if ((rc = s.alloc(&best_idx, sizeof(int32_t) * (size_t)n_phases))) return rc;
+    if ((rc = s.alloc(&cuts, sizeof(int64_t) * (size_t)B * (n_phases + 1)))) return rc;   // + intermediate roundings
+    if ((rc = s.alloc(&best_idx, sizeof(int32_t) * (size_t)(n_phases + 1)))) return rc;
     if ((rc = s.alloc(&rec, sizeof(BestRecord)))) return rc;
     if ((rc = s.alloc(&pbz, (size_t)n)) || (rc = s.alloc(&bz, (size_t)n))) return rc;
     if ((rc = s.alloc(&h, sizeof(float) * n)) || (rc = s.alloc(&side, (size_t)n))) return rc;
@@ -144,24 +154,27 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
     DECO_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
 
     const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    bool first_eval = true;   // the first rounding of the solve initialises the record
+    int64_t* ecuts = cuts + (size_t)B * n_phases;   // intermediate roundings' cuts
     for (int32_t k = 0; k < n_phases; ++k) {
       const deco_phase& ph = phases[k];
       const int32_t C = B * ph.lift;
       InitLaunch il{};
       fill_init(il, g, B, ph.lift, ld, p, seed, k);
       il.y = ybuf[0];
-      if (k == 0) {
+      if (k == 0 || p->phase_init == DECO_PHASE_INIT_FRESH) {
+        // the first phase's initialisation (later phases: draws with phase index k)
         switch (p->init) {
           case DECO_INIT_EXPLICIT: il.x0 = dx0; break;
           case DECO_INIT_MEAN: il.mean = dmean; break;
           case DECO_INIT_DUI:
-            if ((rc = launch_dui(g, k0, k1, 0, h, st))) return rc;
+            if ((rc = launch_dui(g, k0, k1, k, h, st))) return rc;
             kernels += 1;
             il.mean = h;
             break;
           case DECO_INIT_IDI:
           case DECO_INIT_IDI_HALF_UNIFORM:
-            if ((rc = launch_idi(g, idi_threshold(g, p->beta), k0, k1, 0, h, side, st))) return rc;
+            if ((rc = launch_idi(g, idi_threshold(g, p->beta), k0, k1, k, h, side, st))) return rc;
             kernels += 2;
             il.mean = h;
             break;
@@ -181,33 +194,47 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
       int cur = 0;
       PhaseRunner* R = nullptr;
       if ((rc = runners.get(g, C, ld, prec, p->kernel, &R))) return rc;
-      const int32_t main_steps = (prec == DECO_PREC_BF16 && polish) ? ph.steps - p->polish_steps : ph.steps;
-      if ((rc = R->run(ybuf, cur, vbuf, main_steps, p->objective, ph.alpha, ph.momentum, nullptr, nullptr,
-                       mom, mom, flag, st, &kernels)))
-        return rc;
-      if (prec == DECO_PREC_BF16 && polish) {
-        // FP32 polish: widen the BF16 iterate and finish the phase in FP32
-        if ((rc = convert_bf16_to_f32((int64_t)block_elems, ybuf[cur], static_cast<float*>(ybuf[cur ^ 1]), st)))
+      const int32_t T = ph.steps;
+      const int32_t main_steps = (prec == DECO_PREC_BF16 && polish) ? T - p->polish_steps : T;
+      // rounding, cuts and the record (phase best vector only for the final rounding)
+      auto evaluate = [&](int64_t* cut_out, int32_t* idx, uint8_t* phase_best) -> int {
+        int e = launch_pack(g, B, ph.lift, ld, prec, ybuf[cur], zbits, st);
+        if (e) return e;
+        if (p->local_search > 0) {
+          // 1-flip polish of the rounded vectors (off by default)
+          if ((e = launch_local_search(g, B, zbits, p->local_search, ls_gains, ls_changed, st))) return e;
+          kernels += 2 * (int64_t)p->local_search;
+        }
+        if ((e = launch_cut_bits(g, B, zbits, cut_out, st))) return e;
+        if ((e = launch_phase_finish(g, B, k, first_eval, cut_out, zbits, idx, rec, phase_best, bz, st))) return e;
+        first_eval = false;
+        kernels += 5;   // pack, cut, argmax, record, extract
+        return DECO_OK;
+      };
+      // steps in segments that end at the intermediate roundings (every
+      // eval_every steps) and at the switch to the FP32 polish
+      const int32_t E = p->eval_every;
+      for (int32_t s = 0; s < T;) {
+        int32_t next = T;
+        if (E > 0) next = std::min(next, (s / E + 1) * E);
+        if (s < main_steps) next = std::min(next, main_steps);
+        if ((rc = R->run(ybuf, cur, vbuf, next - s, p->objective, ph.alpha, ph.momentum, nullptr, nullptr, mom,
+                         mom, flag, st, &kernels)))
           return rc;
-        kernels += 1;
-        cur ^= 1;
-        prec = DECO_PREC_FP32;
-        if ((rc = runners.get(g, C, ld, prec, p->kernel, &R))) return rc;
-        if ((rc = R->run(ybuf, cur, vbuf, p->polish_steps, p->objective, ph.alpha, ph.momentum, nullptr,
-                         nullptr, mom, mom, flag, st, &kernels)))
-          return rc;
+        s = next;
+        if (E > 0 && s < T && s % E == 0 && (rc = evaluate(ecuts, best_idx + n_phases, nullptr))) return rc;
+        if (s == main_steps && s < T) {
+          // FP32 polish: widen the BF16 iterate and finish the phase in FP32
+          if ((rc = convert_bf16_to_f32((int64_t)block_elems, ybuf[cur], static_cast<float*>(ybuf[cur ^ 1]), st)))
+            return rc;
+          kernels += 1;
+          cur ^= 1;
+          prec = DECO_PREC_FP32;
+          if ((rc = runners.get(g, C, ld, prec, p->kernel, &R))) return rc;
+        }
       }
-      edge_updates += g->nnz * (int64_t)C * ph.steps;
-      int64_t* pc = cuts + (size_t)k * B;
-      if ((rc = launch_pack(g, B, ph.lift, ld, prec, ybuf[cur], zbits, st))) return rc;
-      if (p->local_search > 0) {
-        // 1-flip polish of the rounded vectors (off by default)
-        if ((rc = launch_local_search(g, B, zbits, p->local_search, ls_gains, ls_changed, st))) return rc;
-        kernels += 2 * (int64_t)p->local_search;
-      }
-      if ((rc = launch_cut_bits(g, B, zbits, pc, st))) return rc;
-      if ((rc = launch_phase_finish(g, B, k, pc, zbits, best_idx + k, rec, pbz, bz, st))) return rc;
-      kernels += 5;   // pack, cut, argmax, record, extract
+      edge_updates += g->nnz * (int64_t)C * T;
+      if ((rc = evaluate(cuts + (size_t)k * B, best_idx + k, pbz))) return rc;
     }
     DECO_CUDA_TRY(cudaEventRecord(ev1, st));
 

@@ -1,5 +1,6 @@
 """C-ABI checks that need no GPU: the library loads, exports every function
 include/deco.h declares, and rejects malformed input before any CUDA call."""
+import ctypes
 import os
 import re
 
@@ -35,7 +36,8 @@ def test_every_declared_symbol_is_exported(deco):
     for name in declared:
         assert hasattr(deco.lib, name), name
     assert declared == set(deco.EXPORTED)
-    assert deco.deco_abi_version() == 1
+    assert deco.deco_abi_version() == 2
+    assert ctypes.sizeof(deco.deco_params) == 12 * 4   # the struct of include/deco.h
 
 
 def _csr(n, rows):

@@ -325,6 +325,57 @@ def test_solve_pdeco_schedule(objective):
     assert (res.best_phase, res.best_init) == (ref.best_phase, ref.best_init)
 
 
+def test_solve_intermediate_roundings_match_oracle():
+    # eval_every = 30: roundings after steps 30, 60, 90 of the 120-step phases
+    # (and after 30 of the 40-step ones) compete for the best; the phases'
+    # final roundings, and so the iterates, are those of the plain solve
+    g = gg.er_graph(300, 0.06, 8)
+    B = 96
+    sched = [(1, 120, 0.01, 0.9), (2, 40, 0.001, 0.9), (1, 120, 0.01, 0.9)]
+    G = deco.graph_from(g)
+    plain, _, pc0 = deco.deco_solve(G, B, sched, deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM), 77)
+    res, z, pc = deco.deco_solve(G, B, sched, deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM, eval_every=30), 77)
+    ref = O.solve(g, B, [O.Phase(*s) for s in sched], O.Params(init="idi_half_uniform", eval_every=30), 77)
+    np.testing.assert_array_equal(pc, pc0)   # segmenting a phase does not change its iterate
+    assert res.best_cut >= plain.best_cut and res.best_cut == O.cut_value(g, z)
+    assert res.best_cut == ref.best_cut
+    assert (res.best_phase, res.best_init) == (ref.best_phase, ref.best_init)
+    for k in range(len(sched)):
+        assert _agreement(pc[k], ref.phase_cuts[k]) >= 0.99, k
+
+
+def test_solve_intermediate_roundings_across_the_fp32_polish():
+    # BF16 phases with an FP32 polish of the last 25 steps: roundings every 20
+    # steps fall on both sides of the precision switch; the iterate is the
+    # plain solve's bit for bit
+    g = gg.er_graph(400, 0.05, 3)
+    B = 64
+    sched = [(1, 100, 0.01, 0.9), (2, 50, 0.002, 0.9)]
+    G = deco.graph_from(g)
+    base = dict(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16, polish_steps=25)
+    plain, _, pc0 = deco.deco_solve(G, B, sched, deco.params(**base), 5)
+    res, z, pc = deco.deco_solve(G, B, sched, deco.params(**base, eval_every=20), 5)
+    np.testing.assert_array_equal(pc, pc0)
+    assert res.best_cut >= plain.best_cut and res.best_cut == O.cut_value(g, z)
+
+
+def test_solve_fresh_later_phases_match_oracle():
+    g = gg.er_graph(300, 0.06, 8)
+    B = 96
+    sched = [(1, 120, 0.01, 0.9), (2, 40, 0.001, 0.9), (1, 60, 0.01, 0.9)]
+    G = deco.graph_from(g)
+    for init, oinit in ((deco.DECO_INIT_IDI_HALF_UNIFORM, "idi_half_uniform"), (deco.DECO_INIT_DUI, "dui")):
+        p = deco.params(init=init, phase_init=deco.DECO_PHASE_INIT_FRESH)
+        res, z, pc = deco.deco_solve(G, B, sched, p, 4242)
+        ref = O.solve(g, B, [O.Phase(*s) for s in sched], O.Params(init=oinit, phase_init="fresh"), 4242)
+        assert res.best_cut == O.cut_value(g, z) == ref.best_cut
+        for k in range(len(sched)):
+            assert _agreement(pc[k], ref.phase_cuts[k]) >= 0.99, (oinit, k)
+    with pytest.raises(deco.DecoError):   # an explicit block cannot be drawn afresh
+        deco.deco_solve(G, 4, sched, deco.params(init=deco.DECO_INIT_EXPLICIT, phase_init=1), 0,
+                        x0=gg.uniform_x0(g.n, 4, 0))
+
+
 def test_solve_signed_torus_bf16_polish_cut_gap():
     g = gg.torus_graph(40, 20, 2)
     B = 128

@@ -95,11 +95,12 @@ def test_solve_with_local_search_matches_oracle():
     assert (pc[0] >= pc0[0]).all()
 
 
-def test_local_search_rejected_in_batched_solves():
+@pytest.mark.parametrize("opt", [dict(local_search=5), dict(phase_init=1), dict(eval_every=10)])
+def test_solve_only_options_rejected_in_batched_solves(opt):
     graphs = [gg.ba_graph(60, 4, 1), gg.ba_graph(80, 4, 2)]
     batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs])
     with pytest.raises(deco.DecoError) as ei:
-        deco.deco_solve_batch(batch, 8, deco.params(local_search=5), deco.population(candidates=2, rounds=1), 0)
+        deco.deco_solve_batch(batch, 8, deco.params(**opt), deco.population(candidates=2, rounds=1), 0)
     assert ei.value.status == deco.DECO_ERR_UNSUPPORTED
 
 

@@ -565,3 +565,54 @@ def test_repeated_solve_keeps_an_optimal_warm_start_and_never_loses_ground():
     c1, _ = O.solve_repeated(g, 4, sched, O.Params(init="idi"), 2, 1)
     c3, z3 = O.solve_repeated(g, 4, sched, O.Params(init="idi"), 2, 3)
     assert opt >= c3 >= c1 and O.cut_value(g, z3) == c3
+
+
+# ---------------------------------------------------------------- intermediate roundings, fresh phases
+
+def test_eval_every_beyond_the_phase_changes_nothing():
+    g = gg.er_graph(60, 0.15, 1)
+    ph = [O.Phase(1, 40, 0.01, 0.9), O.Phase(2, 10, 0.002, 0.9)]
+    a = O.solve(g, 16, ph, O.Params(init="idi"), 3)
+    b = O.solve(g, 16, ph, O.Params(init="idi", eval_every=40), 3)
+    assert (a.best_cut, a.best_init, a.best_phase) == (b.best_cut, b.best_init, b.best_phase)
+    for x, y in zip(a.phase_cuts, b.phase_cuts):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_eval_every_best_is_the_best_of_independently_recomputed_roundings():
+    # one phase from an explicit start: the rounding after m E steps is the
+    # rounding of a fresh m E-step run from the same start (the iteration is
+    # deterministic and its momentum starts at zero), so the best over
+    # {m E < T} and the final rounding must be what solve reports, ties to
+    # the earliest rounding, then the lowest start
+    g = gg.er_graph(50, 0.2, 4)
+    B, T, E = 12, 45, 10
+    x0 = gg.uniform_x0(g.n, B, 2)
+    ph = O.Phase(1, T, 0.01, 0.9)
+    res = O.solve(g, B, [ph], O.Params(init="explicit", eval_every=E), 0, x0=x0)
+    Y0 = 2.0 * np.asarray(x0, dtype=np.float64) - 1.0
+    best = None
+    for steps in list(range(E, T, E)) + [T]:
+        cuts = O.cut_values(g, O.binarize(O.run_phase(g, Y0, O.Phase(1, steps, 0.01, 0.9), O.OBJ_MULTILINEAR01), 1))
+        b = int(np.argmax(cuts))
+        if best is None or cuts[b] > best[0]:
+            best = (int(cuts[b]), b)
+    assert (res.best_cut, res.best_init, res.best_phase) == (best[0], best[1], 0)
+    final = O.cut_values(g, O.binarize(O.run_phase(g, Y0, ph, O.OBJ_MULTILINEAR01), 1))
+    np.testing.assert_array_equal(res.phase_cuts[0], final)   # phase cuts stay the final rounding's
+    assert res.best_cut >= int(final.max())
+
+
+def test_fresh_later_phases_do_not_depend_on_earlier_ones():
+    g = gg.er_graph(60, 0.15, 5)
+    p = O.Params(init="idi_half_uniform", phase_init="fresh")
+    a = O.solve(g, 16, [O.Phase(1, 30, 0.01, 0.9), O.Phase(2, 20, 0.002, 0.9)], p, 9)
+    b = O.solve(g, 16, [O.Phase(1, 5, 0.02, 0.0), O.Phase(2, 20, 0.002, 0.9)], p, 9)
+    np.testing.assert_array_equal(a.phase_cuts[1], b.phase_cuts[1])
+    # the default (around the previous best) does depend on them
+    q = O.Params(init="idi_half_uniform")
+    c = O.solve(g, 16, [O.Phase(1, 30, 0.01, 0.9), O.Phase(2, 20, 0.002, 0.9)], q, 9)
+    np.testing.assert_array_equal(c.phase_cuts[0], a.phase_cuts[0])
+    with pytest.raises(ValueError):
+        O.solve(g, 4, [O.Phase(1, 3, 0.01, 0.0), O.Phase(1, 3, 0.01, 0.0)],
+                O.Params(init="explicit", phase_init="fresh"), 0, x0=gg.uniform_x0(g.n, 4, 0))
