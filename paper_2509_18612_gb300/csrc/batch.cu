@@ -6,7 +6,10 @@
 // row -> graph map drives the per-graph IDI thresholds, cut sums, argmax and
 // best records.  Candidate k of the population owns starts
 // [k B/P, (k+1) B/P) and runs T_k steps with alpha_k = 10^{e_k} through the
-// per-column step-size and step-budget arrays of the phase kernels.  Rounds
+// per-column step-size and step-budget arrays of the phase kernels (when
+// every graph's iterate slab fits in shared memory: one on-chip launch whose
+// items are (graph, 128-byte column slab), each graph's replica on chip;
+// otherwise the per-step kernels over the union).  Rounds
 // alternate the lift as listed (Alg. 3); between rounds the host ranks the
 // candidates (sum over graphs of the candidate's best cut) and replaces the
 // bottom half by perturbed copies of the top half.  From a lift's second
@@ -157,6 +160,98 @@ __global__ void k_extract_graphs(int32_t n, int32_t W, const uint32_t* zbits, co
 __global__ void k_fill_ll(int32_t n, long long v, long long* p) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
+}
+
+// One on-chip launch over a batch: item = (graph, column slab), one CTA per
+// item, every member graph's replica and CSR image on chip.  Where the
+// largest member's staging area and momentum do not fit as well, the lean
+// form keeps the momentum in global memory and refreshes the replica from L2.
+struct BatchSlab {
+  bool ok = false;
+  bool lean = false;
+  std::vector<SlabImage> images;
+  SlabGraph* d_graphs = nullptr;
+  int2* d_items = nullptr;
+  unsigned char* xbuf = nullptr;   // lean: 2 x slabs x n x 128 B per graph
+  int32_t n_items = 0, max_n = 0, max_own = 0, max_words = 0;
+  void release() {
+    for (auto& im : images) cudaFree(im.data);
+    images.clear();
+    if (d_graphs) cudaFree(d_graphs);
+    if (d_items) cudaFree(d_items);
+    if (xbuf) cudaFree(xbuf);
+    d_graphs = nullptr;
+    d_items = nullptr;
+    xbuf = nullptr;
+    ok = false;
+  }
+};
+
+// ok stays false (nothing allocated) when a member does not fit on chip
+int batch_slab_prepare(const deco_batch* b, int32_t C, int32_t ld, int prec, void* y, float* v, bool mom_needed,
+                       const float* alpha_cols, const int32_t* steps_cols, BatchSlab* bs) {
+  const deco_graph* U = b->U;
+  const int cols = prec == DECO_PREC_BF16 ? 64 : 32;
+  if (ld % cols) return DECO_OK;
+  const int max_smem = slab_max_smem();
+  int32_t max_n = 0;
+  for (int32_t i = 0; i < b->n_graphs; ++i) max_n = std::max(max_n, b->h_goff[i + 1] - b->h_goff[i]);
+  if ((size_t)max_n * 128 + 4096 > (size_t)max_smem) return DECO_OK;
+  std::vector<SlabGraph> hg((size_t)b->n_graphs);
+  const int32_t slabs = (C + cols - 1) / cols;
+  std::vector<int2> items;
+  const size_t esz = elem_size(prec);
+  for (int32_t i = 0; i < b->n_graphs; ++i) {
+    const int32_t row0 = b->h_goff[i], n = b->h_goff[i + 1] - row0;
+    SlabImage im;
+    int rc = slab_image_rows(U->h_row_ptr.data(), U->h_col.data(), U->h_w.empty() ? nullptr : U->h_w.data(),
+                             U->wmode, row0, n, 1, &im);
+    if (rc) { bs->release(); return rc; }
+    bs->images.push_back(im);
+    bs->max_own = std::max(bs->max_own, im.max_own);
+    bs->max_words = std::max(bs->max_words, im.max_words);
+    SlabGraph& sg = hg[(size_t)i];
+    sg.n = n;
+    sg.ld = ld;
+    sg.C = C;
+    sg.dnet = U->dnet + row0;
+    sg.image = reinterpret_cast<const uint4*>(im.data);
+    std::copy(im.off, im.off + SLAB_MAX_CLUSTER + 1, sg.img_off);
+    std::copy(im.split, im.split + SLAB_MAX_CLUSTER + 1, sg.split);
+    sg.xbuf = nullptr;
+    sg.nslabs = slabs;
+    sg.y = static_cast<unsigned char*>(y) + (size_t)row0 * ld * esz;
+    sg.v = v ? v + (size_t)row0 * ld : nullptr;
+    sg.alpha_cols = alpha_cols;
+    sg.steps_cols = steps_cols;
+    for (int32_t sl = 0; sl < slabs; ++sl) items.push_back(make_int2(i, sl * cols));
+  }
+  bs->max_n = max_n;
+  cudaError_t e = cudaSuccess;
+  if (slab_smem_bytes(max_n, bs->max_own, bs->max_words, prec) > (size_t)max_smem) {
+    if (slab_smem_bytes(max_n, bs->max_own, bs->max_words, prec, true) > (size_t)max_smem || (mom_needed && !v)) {
+      bs->release();
+      return DECO_OK;
+    }
+    bs->lean = true;
+    e = cudaMalloc((void**)&bs->xbuf, (size_t)2 * slabs * U->n * 128);
+    if (e != cudaSuccess) {
+      bs->release();
+      return cuda_fail(e, "cudaMalloc(batch exchange buffer)");
+    }
+    for (int32_t i = 0; i < b->n_graphs; ++i) hg[(size_t)i].xbuf = bs->xbuf + (size_t)2 * slabs * b->h_goff[i] * 128;
+  }
+  e = cudaMalloc((void**)&bs->d_graphs, sizeof(SlabGraph) * hg.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bs->d_items, sizeof(int2) * items.size());
+  if (e == cudaSuccess) e = cudaMemcpy(bs->d_graphs, hg.data(), sizeof(SlabGraph) * hg.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bs->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    bs->release();
+    return cuda_fail(e, "batch on-chip parameters");
+  }
+  bs->n_items = (int32_t)items.size();
+  bs->ok = true;
+  return DECO_OK;
 }
 
 }  // namespace
@@ -373,6 +468,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
     struct Lane {
       int lift = 0;
       PhaseRunner R;
+      BatchSlab S;     // the batched on-chip launch, when every graph fits
       int uses = 0;
       int32_t cap_steps = -1;
       cudaGraphExec_t exec = nullptr;
@@ -385,6 +481,8 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
         for (auto& x : *l) {
           if (x->exec) cudaGraphExecDestroy(x->exec);
           x->R.release(st);
+          cudaStreamSynchronize(st);   // no launch still reads the on-chip parameters
+          x->S.release();
         }
       }
     } cleanup{&lanes, st};
@@ -395,6 +493,12 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
       lanes.emplace_back(new Lane());
       lanes.back()->lift = pop->lifts[i];
       if ((rc = lanes.back()->R.prepare(U, B * pop->lifts[i], ld, p->precision, p->kernel, st))) return rc;
+      const int kind = p->kernel & 0xFF;
+      if ((kind == DECO_KERNEL_AUTO || kind == DECO_KERNEL_ONCHIP) &&
+          (rc = batch_slab_prepare(b, B * pop->lifts[i], ld, p->precision, ybuf[0],
+                                   pop->momentum != 0.0f ? vbuf : nullptr, pop->momentum != 0.0f, alpha_cols,
+                                   steps_cols, &lanes.back()->S)))
+        return rc;
     }
 
     cudaEvent_t ev0, ev1;
@@ -453,8 +557,34 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
       const bool mom = vbuf != nullptr;
       auto body = [&](int64_t* kc) -> int {
         int cur = 0;
-        int e2 = L->R.run(ybuf, cur, vbuf, tmax, p->objective, 0.0f, pop->momentum, alpha_cols, steps_cols, mom,
-                          false, flag, st, kc);
+        int e2 = DECO_OK;
+        if (L->S.ok) {
+          // every graph's slabs in one on-chip launch, in place in ybuf[0]
+          SlabParams sp{};
+          sp.graphs = L->S.d_graphs;
+          sp.items = L->S.d_items;
+          sp.k = 1;
+          sp.threads = 1024;
+          sp.xmode = L->S.lean ? 2 : 0;
+          sp.lean = L->S.lean ? 1 : 0;
+          sp.steps = tmax;
+          const float fac = p->objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
+          sp.alpha = 0.0f;
+          sp.afac = fac;
+          sp.mu = pop->momentum;
+          sp.objective = p->objective;
+          sp.load_v = mom ? 1 : 0;
+          sp.store_v = 0;
+          sp.max_n = L->S.max_n;
+          sp.max_own = L->S.max_own;
+          sp.max_img_words = L->S.max_words;
+          sp.flag = flag;
+          e2 = launch_slab(sp, L->S.n_items, p->precision, U->wmode, st);
+          if (kc) *kc += 1;
+        } else {
+          e2 = L->R.run(ybuf, cur, vbuf, tmax, p->objective, 0.0f, pop->momentum, alpha_cols, steps_cols, mom,
+                        false, flag, st, kc);
+        }
         if (e2) return e2;
         if ((e2 = launch_pack(U, B, lift, ld, p->precision, ybuf[cur], zbits, st))) return e2;
         cudaError_t ce = cudaMemsetAsync(cuts, 0, sizeof(int64_t) * (size_t)G * B, st);
@@ -488,7 +618,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
           if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
         }
         DECO_CUDA_TRY(cudaGraphLaunch(L->exec, st));
-        kernels += (int64_t)(L->R.plan.kernel == KERNEL_ONCHIP ? 1 : tmax) + 5;
+        kernels += (int64_t)(L->S.ok || L->R.plan.kernel == KERNEL_ONCHIP ? 1 : tmax) + 5;
       } else {
         if ((rc = body(&kernels))) return rc;
       }

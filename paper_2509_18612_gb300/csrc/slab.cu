@@ -39,12 +39,15 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline SmemLayout slab_layout(int max_n, int max_own, int max_img_words, int prec) {
+// lean: no staging area (the new rows go through L2) and the momentum in
+// global memory, so that a whole graph of up to ~1 500 rows fits one CTA
+__host__ __device__ inline SmemLayout slab_layout(int max_n, int max_own, int max_img_words, int prec,
+                                                  bool lean) {
   SmemLayout L{};
   size_t o = 0;
   L.rep = o;   o = align16(o + (size_t)max_n * 128);
-  L.stage = o; o = align16(o + (size_t)max_own * 128);
-  L.vsm = o;   o = align16(o + (size_t)max_own * (prec == DECO_PREC_BF16 ? 256 : 128));
+  L.stage = o; o = align16(o + (lean ? 0 : (size_t)max_own * 128));
+  L.vsm = o;   o = align16(o + (lean ? 0 : (size_t)max_own * (prec == DECO_PREC_BF16 ? 256 : 128)));
   L.dn = o;    o = align16(o + (size_t)max_own * 4);
   L.img = o;   o = align16(o + (size_t)max_img_words * 4);
   L.total = o;
@@ -190,7 +193,7 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int PREC, int WMODE, int NT>
+template <int PREC, int WMODE, int NT, bool LEAN>
 __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_xbar;
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   if (P.items) { const int2 it = P.items[item]; gi = it.x; col0 = it.y; }
   const SlabGraph& G = P.graphs ? P.graphs[gi] : P.g0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const SmemLayout L = slab_layout(P.max_n, P.max_own, P.max_img_words, PREC);
+  const SmemLayout L = slab_layout(P.max_n, P.max_own, P.max_img_words, PREC, LEAN);
   uint32_t* rep = reinterpret_cast<uint32_t*>(smem + L.rep);
   uint32_t* stage = reinterpret_cast<uint32_t*>(smem + L.stage);
   float* vsm = reinterpret_cast<float*>(smem + L.vsm);
@@ -228,9 +231,11 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
     for (int i = tid; i < n16; i += NT) reinterpret_cast<uint4*>(img)[i] = src[i];
   }
   for (int i = tid; i < own; i += NT) dn[i] = __ldg(G.dnet + r0 + i);
-  for (int i = tid; i < own * COLS; i += NT) {
-    const int rl = i / COLS, c = i % COLS;
-    vsm[i] = (P.load_v && G.v) ? G.v[(size_t)(r0 + rl) * ld + col0 + c] : 0.0f;
+  if (!LEAN) {
+    for (int i = tid; i < own * COLS; i += NT) {
+      const int rl = i / COLS, c = i % COLS;
+      vsm[i] = (P.load_v && G.v) ? G.v[(size_t)(r0 + rl) * ld + col0 + c] : 0.0f;
+    }
   }
 
   // ---- per-lane column parameters
@@ -259,8 +264,9 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   const bool lap = P.objective == DECO_OBJ_LAPLACIAN;
   const bool mom = P.mu != 0.0f;
   bool bad = false, timed_out = false;
-  // exchange of the new rows between the CTAs of the cluster
-  const int xmode = k == 1 ? XCHG_LOCAL : P.xmode;
+  // exchange of the new rows between the CTAs of the cluster (LEAN: through L2
+  // even for a single CTA, which has no staging area)
+  const int xmode = LEAN ? XCHG_L2 : (k == 1 ? XCHG_LOCAL : P.xmode);
   const int slab = col0 / COLS;
   unsigned char* x0buf = G.xbuf + (size_t)slab * n * 128;
   unsigned char* x1buf = G.xbuf + ((size_t)G.nslabs + slab) * n * 128;
@@ -296,7 +302,8 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
       for (int h = 0; h < (PREC == DECO_PREC_BF16 ? 2 : 1); ++h) {
         const float grad = lap ? fmaf(dr, y[h], -acc[h]) : -acc[h];
         float step = grad;
-        float* vp = vsm + (size_t)rl * COLS + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane);
+        float* vp = LEAN ? G.v + (size_t)r * ld + col0 + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane)
+                         : vsm + (size_t)rl * COLS + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane);
         if (mom) step = fmaf(P.mu, *vp, grad);
         const bool active = t < tmax[h];
         float yn = fmaf(alpha[h], step, y[h]);
@@ -348,7 +355,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
     *reinterpret_cast<uint4*>(yout + (size_t)(r0 + rl) * ld * ESZ + q * 16) =
         reinterpret_cast<const uint4*>(rep)[(size_t)(r0 + rl) * 8 + q];
   }
-  if (P.store_v && G.v) {
+  if (!LEAN && P.store_v && G.v) {
     for (int i = tid; i < own * COLS; i += NT) {
       const int rl = i / COLS, c = i % COLS;
       G.v[(size_t)(r0 + rl) * ld + col0 + c] = vsm[i];
@@ -358,9 +365,9 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   if (timed_out && P.flag) atomicOr(P.flag, 2);
 }
 
-template <int PREC, int WMODE, int NT>
+template <int PREC, int WMODE, int NT, bool LEAN>
 cudaError_t launch_t(const SlabParams& p, int n_items, size_t smem, cudaStream_t st) {
-  auto fn = k_slab<PREC, WMODE, NT>;
+  auto fn = k_slab<PREC, WMODE, NT, LEAN>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
@@ -380,9 +387,14 @@ cudaError_t launch_t(const SlabParams& p, int n_items, size_t smem, cudaStream_t
 
 template <int PREC, int NT>
 cudaError_t launch_n(const SlabParams& p, int wmode, int n_items, size_t smem, cudaStream_t st) {
-  if (wmode == W_UNIT) return launch_t<PREC, W_UNIT, NT>(p, n_items, smem, st);
-  if (wmode == W_SIGN) return launch_t<PREC, W_SIGN, NT>(p, n_items, smem, st);
-  return launch_t<PREC, W_GENERAL, NT>(p, n_items, smem, st);
+  if (p.lean) {
+    if (wmode == W_UNIT) return launch_t<PREC, W_UNIT, 1024, true>(p, n_items, smem, st);
+    if (wmode == W_SIGN) return launch_t<PREC, W_SIGN, 1024, true>(p, n_items, smem, st);
+    return launch_t<PREC, W_GENERAL, 1024, true>(p, n_items, smem, st);
+  }
+  if (wmode == W_UNIT) return launch_t<PREC, W_UNIT, NT, false>(p, n_items, smem, st);
+  if (wmode == W_SIGN) return launch_t<PREC, W_SIGN, NT, false>(p, n_items, smem, st);
+  return launch_t<PREC, W_GENERAL, NT, false>(p, n_items, smem, st);
 }
 
 template <int PREC>
@@ -393,8 +405,8 @@ cudaError_t launch_w(const SlabParams& p, int wmode, int n_items, size_t smem, c
 
 }  // namespace
 
-size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec) {
-  return slab_layout(max_n, max_own, max_img_words, prec).total;
+size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec, bool lean) {
+  return slab_layout(max_n, max_own, max_img_words, prec, lean).total;
 }
 
 int slab_max_smem() {
@@ -423,15 +435,18 @@ void slab_split(const int32_t* row_ptr_host, int32_t n, int k, int32_t* split) {
   split[k] = n;
 }
 
-int slab_image(deco_graph* g, int k, const SlabImage** out) {
-  for (auto& im : g->images) {
-    if (im.k == k) { *out = &im; return DECO_OK; }
-  }
+// On-chip CSR image of rows [row0, row0 + n) of a CSR whose columns in that
+// range refer to the same rows (one member graph of a disjoint union, or a
+// whole graph with row0 = 0), for cluster size k; device memory in im->data.
+int slab_image_rows(const int32_t* row_ptr, const int32_t* col, const float* w, int wmode, int32_t row0,
+                    int32_t n, int k, SlabImage* out) {
   SlabImage im;
   im.k = k;
-  slab_split(g->h_row_ptr.data(), g->n, k, im.split);
-  for (int i = k + 1; i <= SLAB_MAX_CLUSTER; ++i) im.split[i] = g->n;
-  const bool gen = g->wmode == W_GENERAL;
+  std::vector<int32_t> lrp((size_t)n + 1);
+  for (int32_t r = 0; r <= n; ++r) lrp[r] = row_ptr[row0 + r] - row_ptr[row0];
+  slab_split(lrp.data(), n, k, im.split);
+  for (int i = k + 1; i <= SLAB_MAX_CLUSTER; ++i) im.split[i] = n;
+  const bool gen = wmode == W_GENERAL;
   std::vector<uint32_t> words;
   for (int part = 0; part < k; ++part) {
     im.off[part] = (int32_t)(words.size() / 4);
@@ -440,25 +455,25 @@ int slab_image(deco_graph* g, int k, const SlabImage** out) {
     std::vector<uint32_t> offs;
     std::vector<float> wts;
     for (int rl = 0; rl < own; ++rl) {
-      const int r = r0 + rl;
-      const int e0 = g->h_row_ptr[r], e1 = g->h_row_ptr[r + 1];
+      const int r = row0 + r0 + rl;
+      const int e0 = row_ptr[r], e1 = row_ptr[r + 1];
       int np = 0, nn = 0;
       for (int e = e0; e < e1; ++e) {
-        if (g->wmode == W_SIGN && g->h_w[e] < 0.0f) ++nn; else ++np;
+        if (wmode == W_SIGN && w[e] < 0.0f) ++nn; else ++np;
       }
       // positive (or all) entries, then negative entries; device order keeps
       // the positives of a +-1 row first
       info[4 * rl + 0] = (int32_t)offs.size();
       info[4 * rl + 1] = np;
       for (int e = e0; e < e0 + np; ++e) {
-        offs.push_back((uint32_t)g->h_col[e] * 128u);
-        wts.push_back(gen ? g->h_w[e] : 1.0f);
+        offs.push_back((uint32_t)(col[e] - row0) * 128u);
+        wts.push_back(gen ? w[e] : 1.0f);
       }
       while (offs.size() % 4) { offs.push_back(0); wts.push_back(0.0f); }
       info[4 * rl + 2] = (int32_t)offs.size();
       info[4 * rl + 3] = nn;
       for (int e = e0 + np; e < e1; ++e) {
-        offs.push_back((uint32_t)g->h_col[e] * 128u);
+        offs.push_back((uint32_t)(col[e] - row0) * 128u);
         wts.push_back(-1.0f);
       }
       while (offs.size() % 4) { offs.push_back(0); wts.push_back(0.0f); }
@@ -487,13 +502,29 @@ int slab_image(deco_graph* g, int k, const SlabImage** out) {
     cudaFree(im.data);
     return cuda_fail(e, "cudaMemcpy(slab image)");
   }
+  *out = im;
+  return DECO_OK;
+}
+
+int slab_image(deco_graph* g, int k, const SlabImage** out) {
+  for (auto& im : g->images) {
+    if (im.k == k) { *out = &im; return DECO_OK; }
+  }
+  SlabImage im;
+  int rc = slab_image_rows(g->h_row_ptr.data(), g->h_col.data(), g->h_w.empty() ? nullptr : g->h_w.data(),
+                           g->wmode, 0, g->n, k, &im);
+  if (rc) return rc;
   g->images.push_back(im);
   *out = &g->images.back();
   return DECO_OK;
 }
 
 int launch_slab(const SlabParams& p, int n_items, int prec, int wmode, cudaStream_t st) {
-  const size_t smem = slab_smem_bytes(p.max_n, p.max_own, p.max_img_words, prec);
+  if (p.lean && (p.xmode != 2 || (p.mu != 0.0f && !p.load_v))) {
+    set_error("lean slab launch: needs the L2 exchange and momentum loaded from global memory");
+    return DECO_ERR_ARG;
+  }
+  const size_t smem = slab_smem_bytes(p.max_n, p.max_own, p.max_img_words, prec, p.lean != 0);
   if (smem > (size_t)slab_max_smem()) {
     set_error("slab kernel needs %zu bytes of shared memory", smem);
     return DECO_ERR_UNSUPPORTED;

@@ -46,14 +46,19 @@ struct SlabParams {
   int32_t objective;
   int32_t load_v, store_v;
   int32_t max_n, max_own, max_img_words;
+  int32_t lean;                // no staging area, momentum in global memory (needs xmode 2 and load_v)
   int32_t* flag;
 };
 
-size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec);
+size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec, bool lean = false);
 int slab_max_smem();
 void slab_split(const int32_t* row_ptr_host, int32_t n, int k, int32_t* split);
 // builds (or finds) the on-chip CSR image of g for cluster size k
 int slab_image(deco_graph* g, int k, const SlabImage** out);
+// the image of rows [row0, row0 + n) of a host CSR (a member graph of a
+// disjoint union: its columns in the same range), owned by the caller
+int slab_image_rows(const int32_t* row_ptr, const int32_t* col, const float* w, int wmode, int32_t row0,
+                    int32_t n, int k, SlabImage* out);
 int launch_slab(const SlabParams& p, int n_items, int prec, int wmode, cudaStream_t st);
 
 }  // namespace deco

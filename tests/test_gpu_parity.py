@@ -586,6 +586,29 @@ def test_batch_kernels_and_replay_agree():
     assert outs[0] == outs[1]
 
 
+@pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
+@pytest.mark.parametrize("sizes", [(150, 300), (300, 1150)])
+def test_batch_onchip_items_equal_the_union_per_step_kernel(precision, sizes):
+    # 40 graphs whose union does not fit in shared memory while every member
+    # does: the default runs one on-chip launch with an item per (graph,
+    # 128-byte column slab) -- with graphs of up to 1 150 rows in the lean
+    # form (momentum in global memory, replica refreshed from L2); the
+    # per-step kernel over the union performs the same FP32 operations in the
+    # same order
+    rng = np.random.default_rng(77)
+    graphs = [gg.ba_graph(int(n), 4, 700 + i) for i, n in enumerate(rng.integers(sizes[0], sizes[1], 40))]
+    batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs])
+    pop = deco.population(candidates=4, rounds=3, t_lo=20, t_hi=50, e_lo=-2.5, e_hi=-1.5, momentum=0.9,
+                          lifts=(1, 2))
+    outs = []
+    for kernel in (deco.DECO_KERNEL_GLOBAL, deco.DECO_KERNEL_AUTO):
+        p = deco.params(init=deco.DECO_INIT_IDI, precision=precision, kernel=kernel)
+        res, best, ex = deco.deco_solve_batch(batch, 64, p, pop, 9, want_round_cuts=True)
+        outs.append((best.tolist(), ex["round_cuts"].tobytes(), ex["round_scores"].tobytes(), res.kernel_launches))
+    assert outs[0][:3] == outs[1][:3]
+    assert outs[1][3] < outs[0][3]   # one launch per phase instead of one per step
+
+
 def test_batch_rejects_bad_population():
     batch = deco.deco_create_batch([deco.graph_from(gg.ba_graph(50, 4, 1))])
     with pytest.raises(deco.DecoError) as ei:
