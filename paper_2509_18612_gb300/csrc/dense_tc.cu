@@ -386,8 +386,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 // Warp 0 lane 0 loads (TMA); warp 1 lane 0 issues the MMAs of the even chunks
 // of the contraction range into accumulator D0, warp 2 lane 0 those of the odd
 // chunks into D1 (so the wait for one chunk's tiles overlaps the other
-// issuer's MMAs); warps 3-6 run the update on D0 + D1; the stage ring runs on
-// across steps.  Between steps a grid barrier
+// issuer's MMAs); warps 3-10 run the update on D0 + D1 (two warps per lane
+// quarter of tensor memory, each on half of the columns); the stage ring runs
+// on across steps.  Between steps a grid barrier
 // (a counter in global memory, bounded spin) orders the new YT of every CTA
 // before the next step's B tiles are loaded; the A tiles of the next step are
 // requested before that barrier, as A does not change.  The y and V of the
@@ -396,8 +397,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dense_step(const __grid_constan
 // per owning CTA and sent with one bulk shared-memory copy per peer, whose
 // bytes complete the owner's receive barrier.
 
-constexpr int PT = 224;          // threads of the phase kernel
-constexpr int PNV = 8;           // update vectors per thread at most
+constexpr int P_UPD = 256;       // update threads (warps 3 - 10: two warps per tensor-memory lane quarter)
+constexpr int PT = 96 + P_UPD;   // threads of the phase kernel
+constexpr int PNV = 4;           // update vectors per thread at most
 constexpr int P_MAX_SB = 16;     // B stages (one YT tile each)
 constexpr int P_MAX_SA = 5;      // A stages (the streamed A tiles)
 constexpr int P_RESIDENT = 8;    // A chunks kept in tensor memory (8 x 32 columns + two 128-column accumulators)
@@ -536,10 +538,11 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
   const uint32_t tmem = tmem_slot;
   bool timed_out = false;
   if (R > 0 && warp >= 3) {
-    // the resident A tiles: row (TMEM lane) 32 quarter + lane, straight from global memory
-    const int quarter = warp & 3, row = quarter * 32 + lane;
+    // the resident A tiles: row (TMEM lane) 32 quarter + lane, straight from
+    // global memory; the two warps of a quarter take alternate chunks
+    const int quarter = warp & 3, row = quarter * 32 + lane, colhalf = (warp - 3) >> 2;
     const __nv_bfloat16* arow = args.A + (size_t)(m0 + row) * p.kpad;
-    for (int c = 0; c < R; ++c) {
+    for (int c = colhalf; c < R; c += 2) {
       uint32_t v[32];
       const uint4* src = reinterpret_cast<const uint4*>(arow + (size_t)(kb + kr + c) * BK);
 #pragma unroll
@@ -641,6 +644,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     // ---------------- update warps: et = row-vector owner index, quarter = TMEM lanes
     const int et = tid - 96;
     const int quarter = warp & 3;
+    const int colhalf = (warp - 3) >> 2;   // which 32-column chunks of the accumulator this warp stages
     const int row = quarter * 32 + lane;   // tile row read from tensor memory
     const int qown = row / ROWS;
     uint4 yr[PNV];
@@ -649,7 +653,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     int32_t scol[PNV];
 #pragma unroll
     for (int u = 0; u < PNV; ++u) {
-      const int vi = et + 128 * u;
+      const int vi = et + P_UPD * u;
       yr[u] = make_uint4(0, 0, 0, 0);
       acol[u] = 0.0f;
       scol[u] = 0;
@@ -672,13 +676,13 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     bool bad = false;
     for (int t = 0; t < args.steps && !timed_out; ++t) {
       if (KS > 1 && et == 0) mbar_expect_tx(&recv_full, (uint32_t)(KS - 1) * blk_bytes);
-      if (named_sync_or(1, 128, !mbar_wait(&done, (uint32_t)t & 1u))) { timed_out = true; break; }
+      if (named_sync_or(1, P_UPD, !mbar_wait(&done, (uint32_t)t & 1u))) { timed_out = true; break; }
       tc_fence_after();
       // accumulator -> out[owner][c][row % ROWS]
       {
         float* dst = out + (size_t)qown * W * ROWS + (row % ROWS);
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        for (int c0 = 0; c0 < nt; c0 += 32) {
+        for (int c0 = 32 * colhalf; c0 < nt; c0 += 64) {
           float gv[32], g1[32];
           tmem_ld32(tl + (uint32_t)c0, gv);
           if (nloc > 1) {   // D0 + D1
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       }
       tc_fence_before();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged rows -> bulk copy reads
-      named_sync(1, 128);
+      named_sync(1, P_UPD);
       if (KS > 1 && et == 0) {
         for (int q = 0; q < KS; ++q) {
           if (q == r) continue;
@@ -702,14 +706,14 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
-      if (KS > 1 && named_sync_or(1, 128, !mbar_wait_cluster(&recv_full, (uint32_t)t & 1u))) {
+      if (KS > 1 && named_sync_or(1, P_UPD, !mbar_wait_cluster(&recv_full, (uint32_t)t & 1u))) {
         timed_out = true;
         break;
       }
       __nv_bfloat16* YTo = args.yt[(t + 1) & 1];
 #pragma unroll
       for (int u = 0; u < PNV; ++u) {
-        const int vi = et + 128 * u;
+        const int vi = et + P_UPD * u;
         if (vi >= nvec) continue;
         const int c = vi / OCT, o = vi % OCT;
         float acc[8];
@@ -752,7 +756,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       }
       if (KS > 1 && et == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // `out` reusable
       asm volatile("fence.proxy.async.global;" ::: "memory");   // new rows -> the next step's TMA reads
-      named_sync(1, 128);
+      named_sync(1, P_UPD);
       if (et == 0 && t + 1 < args.steps) {
         mbar_arrive_local(&out_free);   // the rings may take the next step's tiles
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(args.gbar) : "memory");
@@ -761,7 +765,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     if (MOM) {
 #pragma unroll
       for (int u = 0; u < PNV; ++u) {
-        const int vi = et + 128 * u;
+        const int vi = et + P_UPD * u;
         if (vi >= nvec || scol[u] < 0) continue;
         const size_t off = (size_t)(cbase + vi / OCT) * p.kpad + i_base + 8 * (vi % OCT);
         *reinterpret_cast<float4*>(p.VT + off) = make_float4(vr[u][0], vr[u][1], vr[u][2], vr[u][3]);
@@ -921,7 +925,7 @@ int dense_phase_shape(int32_t kpad, int32_t cpad, int ks, int w, DensePhaseShape
   const size_t a_st = (size_t)BM * BK * 2, b_st = (size_t)w * BK * 2;
   const long long room = (long long)optin - 1024 - 512 - (long long)recv_b;
   const int nk = kpad / BK;
-  if (w < 32 || w > 128 || w % 32 || ks > nk || (ks & (ks - 1)) || ks > 8 || (w + 8 * ks - 1) / (8 * ks) > PNV ||
+  if (w < 32 || w > 128 || w % 32 || ks > nk || (ks & (ks - 1)) || ks > 8 || (w + 16 * ks - 1) / (16 * ks) > PNV ||
       room <= 0) {
     set_error("dense phase kernel: no shape for w=%d ks=%d", w, ks);
     return DECO_ERR_UNSUPPORTED;
