@@ -129,6 +129,11 @@ typedef enum deco_status {
  * narrow slab of a graph too large for shared memory stays in L2.  Needs
  * ld >= round_up(C, 8 * 2^s). */
 #define DECO_KERNEL_COLUMN_SLABS(s) ((s) << 16)
+/* With DECO_KERNEL_ONCHIP, the lean form: no staging area in shared memory
+ * and the momentum kept in global memory, the new rows exchanged through L2
+ * (also by a single CTA), so that a cluster half as large fits.  Same
+ * iterates as the other forms. */
+#define DECO_KERNEL_LEAN (1 << 20)
 
 /* deco_create_graph flags */
 #define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */

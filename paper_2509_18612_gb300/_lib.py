@@ -47,6 +47,7 @@ DECO_KERNEL_GLOBAL = 1
 DECO_KERNEL_ONCHIP = 2
 DECO_KERNEL_DENSE = 3
 DECO_KERNEL_DENSE_PER_STEP = 1 << 12
+DECO_KERNEL_LEAN = 1 << 20
 
 # every function include/deco.h declares (checked by the CPU test-suite)
 EXPORTED = [

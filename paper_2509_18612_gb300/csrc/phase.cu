@@ -64,7 +64,10 @@ static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int wa
 bool valid_selector(int kernel) {
   const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
   const int s = (kernel >> 16) & 0xF;
-  if (kernel & ~0xFFFFF) return false;
+  const int lean = (kernel >> 20) & 1;
+  if (kernel & ~0x1FFFFF) return false;
+  if (lean && kind != DECO_KERNEL_ONCHIP) return false;
+  if (lean && x == 1) return false;   // the lean form exchanges through L2
   if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_DENSE || t == 3 || x == 3) return false;
   if (x && kind != DECO_KERNEL_ONCHIP) return false;
   if (t && kind != DECO_KERNEL_ONCHIP && !(kind == DECO_KERNEL_DENSE && t == 1)) return false;
@@ -151,6 +154,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_t = (force >> 12) & 0x3;
   const int want_x = (force >> 14) & 0x3;
   const int want_s = (force >> 16) & 0xF;
+  const bool want_lean = ((force >> 20) & 1) != 0;
   force &= 0xFF;
   if (force == DECO_KERNEL_DENSE) {
     // BF16 blocks only; an FP32 block (e.g. the FP32 polish) is planned as AUTO
@@ -159,6 +163,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   }
   plan->threads = want_t == 1 ? 512 : 1024;
   plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
+  plan->lean = want_lean;
   if (force == DECO_KERNEL_GLOBAL) {
     if (want_s) {
       // column slabs of width w, run one after another in a slab-major copy
@@ -189,7 +194,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
     int64_t max_words = 0, max_edges = 0;
     image_sizes(g, k, split, &max_own, &max_words, &max_edges);
     if (max_words > (1 << 26)) continue;
-    const size_t smem = slab_smem_bytes(g->n, max_own, (int)max_words, prec);
+    const size_t smem = slab_smem_bytes(g->n, max_own, (int)max_words, prec, want_lean);
     if (smem > (size_t)max_smem) continue;
     const int per_sm = std::max(1, std::min(4, (int)((size_t)(max_smem + 1024) / (smem + 1024))));
     const int waves = (int)((items * (int64_t)k + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm));
@@ -259,7 +264,7 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
     if (rc) return rc;
     plan.image = *im;
   }
-  if (plan.k > 1 && plan.xmode == 2) {
+  if ((plan.k > 1 && plan.xmode == 2) || plan.lean) {
     const size_t bytes = 2 * (size_t)plan.items * g->n * 128;
     cudaError_t e = cudaMallocAsync((void**)&xbuf, bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(exchange buffer)");
@@ -288,7 +293,8 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     p.items = nullptr;
     p.k = plan.k;
     p.threads = plan.threads;
-    p.xmode = plan.xmode;
+    p.xmode = plan.lean ? 2 : plan.xmode;
+    p.lean = plan.lean ? 1 : 0;
     p.steps = steps;
     const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
     p.alpha = fac * alpha;

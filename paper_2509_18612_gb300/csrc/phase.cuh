@@ -15,6 +15,7 @@ struct PhasePlan {
   int k = 1;                     // cluster size of the on-chip kernel
   int threads = 1024;            // CTA size of the on-chip kernel
   int xmode = 2;                 // exchange between cluster CTAs: 1 DSMEM, 2 L2
+  bool lean = false;             // on-chip kernel: no staging area, momentum in global memory (L2 exchange)
   int col_slabs = 1;             // global kernel: column slabs run one after another (slab-major)
   int slab_w = 0;                // their width
   int items = 0;                 // column slabs

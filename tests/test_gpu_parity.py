@@ -440,8 +440,10 @@ def _run_phase(g, y, v, C, ld, steps, objective, precision, alpha, mu, kernel, a
 
 @pytest.mark.parametrize("name", ["er800", "torus", "ba", "signed", "isolated", "er100"])
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
-@pytest.mark.parametrize("k,xchg", [(0, 0), (1, 0), (2, 0), (4, 0), (8, 0), (2, 1), (4, 1), (8, 1)])
+@pytest.mark.parametrize("k,xchg", [(0, 0), (1, 0), (2, 0), (4, 0), (8, 0), (2, 1), (4, 1), (8, 1),
+                                    (1, 4), (2, 4), (4, 4)])
 def test_onchip_phase_bitwise_equals_global(name, precision, k, xchg):
+    # xchg 4: the lean form (momentum in global memory, rows through L2)
     g = GRAPHS[name]()
     cols = 64 if precision == deco.DECO_PREC_BF16 else 32
     C = 3 * cols - 5                                # three slabs, ragged last slab
@@ -453,7 +455,9 @@ def test_onchip_phase_bitwise_equals_global(name, precision, k, xchg):
     alpha_cols = to_dev(np.random.default_rng(2).uniform(1e-3, 2e-2, C).astype(np.float32))
     ref_y, ref_v, f0 = _run_phase(g, y, v, C, ld, 9, objective, precision, 0.0, mu, deco.DECO_KERNEL_GLOBAL,
                                   alpha_cols, steps_cols)
-    sel = deco.DECO_KERNEL_ONCHIP | (k << 8) | (xchg << 14)   # xchg 1: DSMEM broadcast, 0: L2 (default)
+    sel = deco.DECO_KERNEL_ONCHIP | (k << 8) | ((xchg & 3) << 14)   # xchg 1: DSMEM broadcast, 0: L2 (default)
+    if xchg == 4:
+        sel |= deco.DECO_KERNEL_LEAN
     try:
         got_y, got_v, f1 = _run_phase(g, y, v, C, ld, 9, objective, precision, 0.0, mu, sel, alpha_cols, steps_cols)
     except deco.DecoError as e:
