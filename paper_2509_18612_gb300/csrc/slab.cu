@@ -10,7 +10,9 @@
 //     memory, so every neighbour gather is a conflict-free 128-byte row read
 //     (lane l reads word l of row j: one shared-memory wavefront per edge);
 //   * the rows are split between the k CTAs by gather cost; each CTA keeps its
-//     own rows' CSR image, momentum and a staging area in shared memory;
+//     own rows' CSR image, momentum and a staging area in shared memory (the
+//     lean form keeps only the CSR image: momentum in global memory, new rows
+//     through L2, so that larger graphs or smaller clusters fit);
 //   * per step: gather + fused update of the own rows into the staging area,
 //     cluster barrier, broadcast of the staged rows into all k replicas
 //     through distributed shared memory, cluster barrier.
