@@ -666,9 +666,24 @@ def profile_kernel(sel: int, precision: str, workload: str = "er800"):
     for ncu captures (capture the second launch).
       er800:  one 800-step unlifted phase of ER(800, 0.06), C = 1024, mu = 0.9
       er1m:   two steps of ER(10^6, avg degree 10), C = 128, mu = 0
-      er4096: four steps of ER(4096, 0.5), C = 128, mu = 0"""
+      er4096: four steps of ER(4096, 0.5), C = 128, mu = 0
+      ba32:   the batched on-chip launch of a population round over 32 BA
+              graphs (n ~ U{200..1200}, m = 4; the config-3 family), B = 256,
+              32 candidates, T = 100, mu = 0.9 (the selector is not used)"""
     import torch
     import paper_2509_18612_gb300 as deco
+    if workload == "ba32":
+        rng = np.random.default_rng(3000)
+        gsb = [gg.ba_graph(int(n), 4, 3000 + i) for i, n in enumerate(rng.integers(200, 1201, 32))]
+        batch = deco.deco_create_batch([deco.graph_from(g) for g in gsb])
+        pop = deco.population(candidates=32, rounds=1, t_lo=100, t_hi=100, e_lo=-3.0, e_hi=-1.5, momentum=0.9,
+                              lifts=(1,))
+        pb = deco.params(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16 if precision == "bf16"
+                         else deco.DECO_PREC_FP32)
+        for i in range(2):
+            res, _, _ = deco.deco_solve_batch(batch, 256, pb, pop, 5 + i)
+            print(json.dumps({"launch": i, "device_ms": res.device_ms, "launches": res.kernel_launches}))
+        return
     if workload == "er1m":
         g, C, steps, mu = er1m_graph(), ER1M_B, 2, 0.0
     elif workload == "er4096":
@@ -697,7 +712,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-kernel", type=lambda s: int(s, 0), default=None,
                     help="run only the dominant kernel twice with this launch-shape selector")
-    ap.add_argument("--profile-workload", default="er800", choices=["er800", "er1m", "er4096"])
+    ap.add_argument("--profile-workload", default="er800", choices=["er800", "er1m", "er4096", "ba32"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

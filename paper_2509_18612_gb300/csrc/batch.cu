@@ -224,8 +224,18 @@ int batch_slab_prepare(const deco_batch* b, int32_t C, int32_t ld, int prec, voi
     sg.v = v ? v + (size_t)row0 * ld : nullptr;
     sg.alpha_cols = alpha_cols;
     sg.steps_cols = steps_cols;
-    for (int32_t sl = 0; sl < slabs; ++sl) items.push_back(make_int2(i, sl * cols));
   }
+  // items in decreasing order of their graph's work (stored entries plus
+  // rows): CTAs start in item order, so the last wave holds the small graphs
+  std::vector<int32_t> order((size_t)b->n_graphs);
+  for (int32_t i = 0; i < b->n_graphs; ++i) order[(size_t)i] = i;
+  auto work = [&](int32_t i) {
+    const int32_t r0 = b->h_goff[i], r1 = b->h_goff[i + 1];
+    return (int64_t)(U->h_row_ptr[r1] - U->h_row_ptr[r0]) + 8LL * (r1 - r0);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return work(a) > work(c); });
+  for (int32_t i : order)
+    for (int32_t sl = 0; sl < slabs; ++sl) items.push_back(make_int2(i, sl * cols));
   bs->max_n = max_n;
   cudaError_t e = cudaSuccess;
   if (slab_smem_bytes(max_n, bs->max_own, bs->max_words, prec) > (size_t)max_smem) {

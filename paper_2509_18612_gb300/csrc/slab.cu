@@ -284,6 +284,14 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   for (int t = 0; t < P.steps; ++t) {
     for (int rl = wr0; rl < wr1; ++rl) {
       const int4 ri = rinfo[rl];
+      // LEAN: the row's momentum comes from global memory; its load is issued
+      // before the gather so that its latency hides behind it
+      float vg[2] = {0.0f, 0.0f};
+      if (LEAN && mom) {
+        const float* vrow = G.v + (size_t)(r0 + rl) * ld + col0 + (PREC == DECO_PREC_BF16 ? 2 * lane : lane);
+        vg[0] = vrow[0];
+        if (PREC == DECO_PREC_BF16) vg[1] = vrow[1];
+      }
       float acc[2] = {0.0f, 0.0f};
       if (PREC == DECO_PREC_FP32) {
         acc[0] = gather_f32<+1, GEN>(lb, offs + ri.x, wts + ri.x, ri.y, 0.0f);
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
         float step = grad;
         float* vp = LEAN ? G.v + (size_t)r * ld + col0 + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane)
                          : vsm + (size_t)rl * COLS + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane);
-        if (mom) step = fmaf(P.mu, *vp, grad);
+        if (mom) step = fmaf(P.mu, LEAN ? vg[h] : *vp, grad);
         const bool active = t < tmax[h];
         float yn = fmaf(alpha[h], step, y[h]);
         if (active && !isfinite(yn)) bad = true;
