@@ -542,6 +542,30 @@ int deco_local_search(const deco_graph* g, int32_t B, uint8_t* z, int32_t max_ro
  * Errors: DECO_ERR_ARG, DECO_ERR_TIMEOUT (a wait gave up, 1 s), CUDA. */
 int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, float* ns_per_instruction, void* stream);
 
+/* Failure detection of the bounded device waits.  Every spin-wait of the
+ * kernels (the on-chip kernel's exchange wait, the dense kernels' mbarrier
+ * waits and grid barrier) gives up after 2 s, sets bit 1 of the call's error
+ * flag and lets the kernel return, so that a solve reports DECO_ERR_TIMEOUT
+ * and the CUDA context stays usable.  This probe runs one of those waits, in a
+ * one-thread kernel, on something nothing ever completes:
+ *   which 0  the dense kernels' mbarrier wait (an mbarrier nobody arrives at)
+ *   which 1  the dense phase kernel's grid barrier (a counter nobody increments)
+ *   which 2  the on-chip kernel's exchange wait (an mbarrier nobody arrives at)
+ * waited_ms (host, or NULL) receives the kernel's duration (CUDA events).
+ * Returns DECO_ERR_TIMEOUT when the wait gave up (the expected outcome; the
+ * message gives the time), DECO_OK if it did not.  No paper counterpart.
+ * Synchronises the stream.  Errors: DECO_ERR_ARG, DECO_ERR_OOM, CUDA. */
+int deco_probe_wait_timeout(int32_t which, float* waited_ms, void* stream);
+
+/* Host-side fault injection for tests of the error paths: the k-th scratch
+ * allocation after this call (k >= 1; the stream-ordered temporary buffers
+ * that deco_solve, deco_solve_batch, deco_round_cut and the other calls take
+ * for one call) fails with DECO_ERR_OOM, as a failed cudaMallocAsync would;
+ * the calls must release what they took and leave graphs, batches and the
+ * CUDA context usable.  k = 0 disarms it.  Process-wide, not thread-safe
+ * against concurrent calls.  No paper counterpart.  Errors: DECO_ERR_ARG. */
+int deco_debug_fail_scratch_alloc(int32_t k);
+
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);
 

@@ -58,7 +58,8 @@ EXPORTED = [
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_solve_budget", "deco_greedy", "deco_local_search",
-    "deco_probe_mma_rate", "deco_last_error", "deco_abi_version",
+    "deco_probe_mma_rate", "deco_probe_wait_timeout", "deco_debug_fail_scratch_alloc", "deco_last_error",
+    "deco_abi_version",
 ]
 
 
@@ -142,6 +143,8 @@ def _load():
         "deco_greedy": (ctypes.c_int, [P, I32, U64, P, P, P]),
         "deco_local_search": (ctypes.c_int, [P, I32, P, I32, P, P, P]),
         "deco_probe_mma_rate": (ctypes.c_int, [I32, I32, I32, P, P]),
+        "deco_probe_wait_timeout": (ctypes.c_int, [I32, P, P]),
+        "deco_debug_fail_scratch_alloc": (ctypes.c_int, [I32]),
         "deco_last_error": (ctypes.c_char_p, []),
         "deco_abi_version": (ctypes.c_int, []),
     }
@@ -327,6 +330,22 @@ def deco_probe_mma_rate(n: int = 128, issuers: int = 1, count: int = 4096, strea
     ns = ctypes.c_float()
     _check(lib.deco_probe_mma_rate(int(n), int(issuers), int(count), ctypes.byref(ns), _stream(stream)))
     return ns.value
+
+
+def deco_probe_wait_timeout(which: int, stream=None):
+    """Run one of the kernels' bounded waits on something that never completes
+    (0 dense mbarrier, 1 dense grid barrier, 2 on-chip exchange mbarrier);
+    returns (status, waited ms).  DECO_ERR_TIMEOUT is the expected status."""
+    ms = ctypes.c_float()
+    st = lib.deco_probe_wait_timeout(int(which), ctypes.byref(ms), _stream(stream))
+    if st not in (DECO_OK, DECO_ERR_TIMEOUT):
+        _check(st)
+    return st, ms.value
+
+
+def deco_debug_fail_scratch_alloc(k: int):
+    """Fail the k-th scratch allocation from now on with DECO_ERR_OOM (0 disarms)."""
+    _check(lib.deco_debug_fail_scratch_alloc(int(k)))
 
 
 def deco_set_tuning(g: Graph, C: int, precision: int, kernel: int):

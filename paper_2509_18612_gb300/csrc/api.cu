@@ -35,6 +35,20 @@ static int check_step_args(const deco_graph* g, int32_t C, int32_t ld, const dec
   return DECO_OK;
 }
 
+namespace deco {
+std::atomic<int> g_scratch_fail_countdown{0};
+}
+
+extern "C" int deco_debug_fail_scratch_alloc(int32_t k) {
+  clear_error();
+  if (k < 0) {
+    set_error("k must be >= 0");
+    return DECO_ERR_ARG;
+  }
+  g_scratch_fail_countdown.store(k);
+  return DECO_OK;
+}
+
 extern "C" int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void* y_out,
                          float* v, const deco_step_args* a, int32_t* nonfinite_flag, void* stream) {
   clear_error();

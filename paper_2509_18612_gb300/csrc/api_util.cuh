@@ -2,11 +2,17 @@
 // scratch allocation, pointer kind detection.
 #pragma once
 
+#include <atomic>
 #include <vector>
 
 #include "deco_internal.cuh"
 
 namespace deco {
+
+// Host-side fault injection (deco_debug_fail_scratch_alloc): while positive,
+// every scratch allocation counts it down, and the one that brings it to zero
+// fails with DECO_ERR_OOM instead of allocating.
+extern std::atomic<int> g_scratch_fail_countdown;
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -47,6 +53,11 @@ struct Scratch {
   }
   template <typename T>
   int alloc(T** out, size_t bytes) {
+    if (g_scratch_fail_countdown.load(std::memory_order_relaxed) > 0 &&
+        g_scratch_fail_countdown.fetch_sub(1, std::memory_order_relaxed) == 1) {
+      set_error("injected scratch allocation failure");
+      return DECO_ERR_OOM;
+    }
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(&p, bytes, st);

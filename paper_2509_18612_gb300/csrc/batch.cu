@@ -525,6 +525,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
     std::vector<int32_t> h_steps(Cmax);
     std::vector<int64_t> h_cuts((size_t)G * B);
     for (int32_t r = 0; r < pop->rounds; ++r) {
+      NvtxRange r_round("deco batch round");
       const int32_t lift = pop->lifts[r % pop->n_lifts];
       const int32_t C = B * lift;
       int32_t tmax = 0;

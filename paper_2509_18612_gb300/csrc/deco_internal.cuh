@@ -12,7 +12,20 @@
 
 #include "deco.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace deco {
+
+// NVTX range on the calling host thread for the lifetime of the object (the
+// enqueue of a solve, a phase, its steps and its rounding), so that a
+// profiler can attribute the kernels of each part (ncu --nvtx); without a
+// tool attached the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);

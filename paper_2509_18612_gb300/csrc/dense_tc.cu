@@ -472,6 +472,16 @@ __device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// wait until the grid barrier counter reaches target; false after WAIT_NS
+__device__ __forceinline__ bool grid_wait(const unsigned int* gbar, uint32_t target) {
+  bool ok = ld_acquire(gbar) >= target;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 0; !ok && i < (1u << 30); ++i) {
+    ok = ld_acquire(gbar) >= target;
+    if ((i & 63u) == 0 && gtimer() - t0 > WAIT_NS) break;
+  }
+  return ok;
+}
 
 template <bool MOM, bool LAP, int KS>
 __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ PhaseArgs args) {
@@ -590,14 +600,7 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
       if (timed_out) break;
       if (t > 0) {
         // grid barrier: every CTA has written its rows of the iterate of step t
-        const uint32_t target = (uint32_t)args.ncta * (uint32_t)t;
-        bool ok = ld_acquire(args.gbar) >= target;
-        const uint64_t t0 = gtimer();
-        for (uint32_t i = 0; !ok && i < (1u << 30); ++i) {
-          ok = ld_acquire(args.gbar) >= target;
-          if ((i & 63u) == 0 && gtimer() - t0 > WAIT_NS) break;
-        }
-        if (!ok) { timed_out = true; break; }
+        if (!grid_wait(args.gbar, (uint32_t)args.ncta * (uint32_t)t)) { timed_out = true; break; }
         asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
       }
       for (int kc = 0; kc < nloc; ++kc) {
@@ -903,6 +906,24 @@ int stages_for(int ntmax) {
   return std::max(2, std::min(MAX_STAGES, (int)(RING_BUDGET / stage)));
 }
 
+// Wait-timeout probe: the kernels' own bounded waits on something that never
+// completes -- (0) a CTA mbarrier nobody arrives at, (1) the grid barrier
+// counter nobody increments.  The wait gives up after WAIT_NS and the kernel
+// reports it in bit 1 of *flag, as the dense kernels do.
+__global__ void k_probe_wait(int which, unsigned int* counter, int32_t* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  bool ok;
+  if (which == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ok = mbar_wait(&bar, 0);
+  } else {
+    ok = grid_wait(counter, 1u);
+  }
+  if (!ok) atomicOr(flag, 2);
+}
+
 }  // namespace
 
 int dense_make_maps(const __nv_bfloat16* A, int32_t kpad, __nv_bfloat16* const yt[2], int32_t cpad, int w,
@@ -1107,6 +1128,12 @@ int launch_dense_step(const DenseStep& p, const DenseMaps& maps, int which, cuda
   cudaError_t e = cudaLaunchKernelEx(&cfg, fn, args);
   if (e != cudaSuccess) return cuda_fail(e, "dense step launch");
   return DECO_OK;
+}
+
+int launch_wait_probe_dense(int which, unsigned int* counter, int32_t* flag, cudaStream_t st) {
+  k_probe_wait<<<1, 32, 0, st>>>(which, counter, flag);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DECO_OK : cuda_fail(e, "wait probe launch");
 }
 
 }  // namespace deco

@@ -68,5 +68,9 @@ int dense_from_t(const void* yt, int32_t kpad, int32_t C, void* y, int32_t n, in
                  cudaStream_t st);
 // one step: YT = yt[which] -> YTout = yt[which ^ 1] (p.YT / p.YTout must match)
 int launch_dense_step(const DenseStep& p, const DenseMaps& maps, int which, cudaStream_t st);
+// one thread waits, with the dense kernels' bounded waits, on something that
+// never completes: which 0 a CTA mbarrier, 1 the grid barrier counter
+// (*counter must be 0); sets bit 1 of *flag when the wait gives up
+int launch_wait_probe_dense(int which, unsigned int* counter, int32_t* flag, cudaStream_t st);
 
 }  // namespace deco

@@ -134,3 +134,42 @@ extern "C" int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, fl
   *ns_per_instruction = (float)(sum / sms / ((double)count * issuers));
   return DECO_OK;
 }
+
+extern "C" int deco_probe_wait_timeout(int32_t which, float* waited_ms, void* stream) {
+  clear_error();
+  if (which < 0 || which > 2) {
+    set_error("bad wait kind %d", which);
+    return DECO_ERR_ARG;
+  }
+  cudaStream_t st = as_stream(stream);
+  Scratch s(st);
+  int32_t* d = nullptr;   // [0] the flag, [1] the counter nobody increments
+  int rc = s.alloc((void**)&d, 2 * sizeof(int32_t));
+  if (rc) return rc;
+  DECO_CUDA_TRY(cudaMemsetAsync(d, 0, 2 * sizeof(int32_t), st));
+  cudaEvent_t ev[2];
+  DECO_CUDA_TRY(cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return cuda_fail(cudaGetLastError(), "event");
+  }
+  cudaEventRecord(ev[0], st);
+  rc = which == 2 ? launch_wait_probe_slab(d, st)
+                  : launch_wait_probe_dense(which, reinterpret_cast<unsigned int*>(d + 1), d, st);
+  cudaEventRecord(ev[1], st);
+  int32_t flag = 0;
+  cudaError_t e = rc ? cudaSuccess : cudaMemcpyAsync(&flag, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  if (waited_ms) *waited_ms = ms;
+  if (flag & 2) {
+    set_error("wait probe %d: the bounded wait gave up after %.1f ms", which, ms);
+    return DECO_ERR_TIMEOUT;
+  }
+  return DECO_OK;
+}

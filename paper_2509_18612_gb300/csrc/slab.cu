@@ -151,7 +151,8 @@ __device__ __forceinline__ void gather_bf16(const unsigned char* lb, const uint3
 // ---- exchange helpers (inline PTX: mbarrier, bulk async copy, proxy fences)
 enum { XCHG_LOCAL = 0, XCHG_DSMEM = 1, XCHG_L2 = 2 };
 constexpr uint32_t XCHG_CHUNK = 32768;
-constexpr uint32_t XCHG_SPIN_LIMIT = 1u << 24;   // bounded wait: far above any real copy time
+constexpr uint32_t XCHG_SPIN_LIMIT = 1u << 24;        // bounded wait: far above any real copy time ...
+constexpr uint64_t XCHG_WAIT_NS = 2000000000ull;     // ... and 2 s at most
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -182,10 +183,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // wait for the phase with the given parity to complete; false after the limit
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < XCHG_SPIN_LIMIT; ++i)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 1; i < XCHG_SPIN_LIMIT; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0 && gtimer() - t0 > XCHG_WAIT_NS) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -413,6 +423,16 @@ cudaError_t launch_w(const SlabParams& p, int wmode, int n_items, size_t smem, c
                            : launch_n<PREC, 512>(p, wmode, n_items, smem, st);
 }
 
+// Wait-timeout probe: the exchange wait of k_slab on an mbarrier nobody
+// arrives at; gives up after its limit and reports it in bit 1 of *flag.
+__global__ void k_probe_xchg_wait(int32_t* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0)) atomicOr(flag, 2);
+}
+
 }  // namespace
 
 size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec, bool lean) {
@@ -543,6 +563,12 @@ int launch_slab(const SlabParams& p, int n_items, int prec, int wmode, cudaStrea
                                          : launch_w<DECO_PREC_FP32>(p, wmode, n_items, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "k_slab launch");
   return DECO_OK;
+}
+
+int launch_wait_probe_slab(int32_t* flag, cudaStream_t st) {
+  k_probe_xchg_wait<<<1, 32, 0, st>>>(flag);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DECO_OK : cuda_fail(e, "wait probe launch");
 }
 
 }  // namespace deco

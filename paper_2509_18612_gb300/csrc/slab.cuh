@@ -52,6 +52,9 @@ struct SlabParams {
 
 size_t slab_smem_bytes(int max_n, int max_own, int max_img_words, int prec, bool lean = false);
 int slab_max_smem();
+// one thread waits, with k_slab's bounded exchange wait, on an mbarrier that
+// never completes; sets bit 1 of *flag when the wait gives up
+int launch_wait_probe_slab(int32_t* flag, cudaStream_t st);
 void slab_split(const int32_t* row_ptr_host, int32_t n, int k, int32_t* split);
 // builds (or finds) the on-chip CSR image of g for cluster size k
 int slab_image(deco_graph* g, int k, const SlabImage** out);

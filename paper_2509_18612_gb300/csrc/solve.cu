@@ -150,6 +150,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
       if ((rc = runners.get(g, B * phases[k].lift, ld, prec0, p->kernel, &R))) return rc;
       if (polish && (rc = runners.get(g, B * phases[k].lift, ld, DECO_PREC_FP32, p->kernel, &R))) return rc;
     }
+    NvtxRange r_solve("deco_solve");
     DECO_CUDA_TRY(cudaEventRecord(ev0, st));
     DECO_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
 
@@ -158,6 +159,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
     int64_t* ecuts = cuts + (size_t)B * n_phases;   // intermediate roundings' cuts
     for (int32_t k = 0; k < n_phases; ++k) {
       const deco_phase& ph = phases[k];
+      NvtxRange r_phase(ph.lift > 1 ? "deco phase (lifted)" : "deco phase (unlifted)");
       const int32_t C = B * ph.lift;
       InitLaunch il{};
       fill_init(il, g, B, ph.lift, ld, p, seed, k);
@@ -198,6 +200,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
       const int32_t main_steps = (prec == DECO_PREC_BF16 && polish) ? T - p->polish_steps : T;
       // rounding, cuts and the record (phase best vector only for the final rounding)
       auto evaluate = [&](int64_t* cut_out, int32_t* idx, uint8_t* phase_best) -> int {
+        NvtxRange r_eval("deco round + cut + argmax");
         int e = launch_pack(g, B, ph.lift, ld, prec, ybuf[cur], zbits, st);
         if (e) return e;
         if (p->local_search > 0) {
@@ -218,6 +221,7 @@ extern "C" int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phas
         int32_t next = T;
         if (E > 0) next = std::min(next, (s / E + 1) * E);
         if (s < main_steps) next = std::min(next, main_steps);
+        NvtxRange r_steps("deco steps");
         if ((rc = R->run(ybuf, cur, vbuf, next - s, p->objective, ph.alpha, ph.momentum, nullptr, nullptr, mom,
                          mom, flag, st, &kernels)))
           return rc;

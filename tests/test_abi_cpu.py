@@ -108,3 +108,10 @@ def test_valid_graph_without_gpu_reports_cuda_error(deco):
     with pytest.raises(deco.DecoError) as ei:
         deco.graph_from(g)
     assert ei.value.status in (deco.DECO_ERR_CUDA, deco.DECO_ERR_OOM)
+
+
+def test_fault_injection_hook_arguments(deco):
+    with pytest.raises(deco.DecoError) as ei:
+        deco.deco_debug_fail_scratch_alloc(-1)
+    assert ei.value.status == deco.DECO_ERR_ARG
+    deco.deco_debug_fail_scratch_alloc(0)

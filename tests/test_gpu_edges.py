@@ -1,7 +1,8 @@
 """Degenerate and boundary cases of the solver through the C ABI, against the
 oracle: a single node, an edgeless graph, one starting point, phases of zero
 steps, a lift of three (Eq. 11 summed in order), complete graphs (closed-form
-optimum), and a graph near the shared-memory limit of the on-chip kernel."""
+optimum), a graph near the shared-memory limit of the on-chip kernel, and the
+bounded device waits giving up (failure detection without a GPU fault)."""
 import numpy as np
 import pytest
 
@@ -97,3 +98,56 @@ def test_graph_near_the_shared_memory_limit_on_chip_equals_global(precision):
         torch.cuda.synchronize()
         outs.append((y, v))
     assert torch.equal(outs[0][0][:, :C], outs[1][0][:, :C]) and torch.equal(outs[0][1][:, :C], outs[1][1][:, :C])
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(which):
+    """Failure detection without a GPU fault: one of the kernels' own bounded
+    waits (dense mbarrier wait, dense grid barrier, on-chip exchange wait)
+    runs on something nothing ever completes.  It must give up after its 2 s
+    limit, report DECO_ERR_TIMEOUT through the error flag, and leave the
+    context usable: a solve right after it matches the oracle."""
+    status, ms = deco.deco_probe_wait_timeout(which)
+    assert status == deco.DECO_ERR_TIMEOUT, deco.last_error()
+    # the dense waits give up on the 2 s clock; the on-chip exchange wait on
+    # the clock or on its iteration cap, whichever comes first
+    assert (1900.0 if which < 2 else 1.0) <= ms <= 6000.0, ms
+    assert "gave up" in deco.last_error()
+    g = gg.er_graph(100, 0.1, 0)
+    x0 = gg.uniform_x0(g.n, 16, 0)
+    res, z, pc = deco.deco_solve(deco.graph_from(g), 16, [(1, 50, 0.01, 0.0)],
+                                 deco.params(init=deco.DECO_INIT_EXPLICIT), 0, x0=x0)
+    ref = O.solve(g, 16, [O.Phase(1, 50, 0.01, 0.0)], O.Params(init="explicit"), 0, x0=x0)
+    assert res.best_cut == O.cut_value(g, z)
+    assert _agree(pc[0], ref.phase_cuts[0]) >= 0.99
+
+
+def test_injected_scratch_allocation_failures_leave_the_library_usable():
+    """Host-side fault injection: the k-th scratch allocation of a solve fails
+    with DECO_ERR_OOM (k = 1, 2, ... until the solve needs fewer); each failed
+    call releases what it took, and the next call, on the same graph handle,
+    gives the same result as before the failures."""
+    g = gg.er_graph(100, 0.1, 0)
+    G = deco.graph_from(g)
+    x0 = gg.uniform_x0(g.n, 16, 1)
+    sched = [(1, 30, 0.01, 0.9), (2, 10, 0.001, 0.9)]
+    p = deco.params(init=deco.DECO_INIT_EXPLICIT)
+    base, zb, pcb = deco.deco_solve(G, 16, sched, p, 0, x0=x0)
+    failed = 0
+    try:
+        for k in range(1, 64):
+            deco.deco_debug_fail_scratch_alloc(k)
+            try:
+                res, z, pc = deco.deco_solve(G, 16, sched, p, 0, x0=x0)
+            except deco.DecoError as e:
+                assert e.status == deco.DECO_ERR_OOM and "injected" in str(e), str(e)
+                failed += 1
+                deco.deco_debug_fail_scratch_alloc(0)
+                res, z, pc = deco.deco_solve(G, 16, sched, p, 0, x0=x0)
+                assert res.best_cut == base.best_cut and (pc == pcb).all() and (z == zb).all()
+            else:
+                assert res.best_cut == base.best_cut and (pc == pcb).all()
+                break
+    finally:
+        deco.deco_debug_fail_scratch_alloc(0)
+    assert failed >= 10, failed

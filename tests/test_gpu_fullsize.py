@@ -2,18 +2,18 @@
 times (the autotuner's choice for every block shape), on outputs the oracle
 can compute one by one:
 
-  * config 2 (ER(800, 0.06) and the 40 x 20 torus, B = 1024, pDECO T = 2000):
+  * the main workload (ER(800, 0.06) and the 40 x 20 torus, B = 1024, pDECO T = 2000):
     the first phase's starting points are independent, so the oracle runs a
     sample of 128 of them per graph through the 800 unlifted steps; rounded
     cuts identical on >= 99 % of the sampled (graph, start) pairs;
-  * config 3 (256 BA graphs, B = 256, population 32 x 8): the first round's
+  * the batched workload (256 BA graphs, B = 256, population 32 x 8): the first round's
     columns are independent given the seeded population, so the oracle runs
     64 sampled columns of four graphs; >= 99 % identical;
-  * config 4 sparse (ER, n = 10^6, average degree 10, B = 128, BF16): the IDI
+  * the large sparse workload (ER, n = 10^6, average degree 10, B = 128, BF16): the IDI
     mean bit-exact in full; one step from a dyadic block (every partial sum
     exact in FP32) on 1024 sampled rows within one bf16 rounding; rounding and
     cuts of that block bit-exact in full;
-  * config 5 (BA(2000, 4), ER(5000, 0.002)): the network's proposal within
+  * the learned proposal's evaluation graphs (BA(2000, 4), ER(5000, 0.002)): the network's proposal within
     1e-5 of the oracle's at every node.
 """
 import numpy as np
@@ -35,7 +35,7 @@ DEV = torch.device("cuda:0")
 MUL = deco.DECO_OBJ_MULTILINEAR01
 
 
-def test_config2_first_phase_sampled_starts():
+def test_er800_torus_b1024_first_phase_sampled_starts():
     sched = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)] * 2
     B, same, total = 1024, 0, 0
     for g, seed in ((gg.er_graph(800, 0.06, 1), 11), (gg.torus_graph(40, 20, 2), 12)):
@@ -53,7 +53,7 @@ def test_config2_first_phase_sampled_starts():
     assert same >= 0.99 * total, (same, total)
 
 
-def test_config3_first_round_sampled_columns():
+def test_ba256_batch_first_round_sampled_columns():
     rng = np.random.default_rng(3000)
     sizes = rng.integers(200, 1201, 256)
     graphs = [gg.ba_graph(int(n), 4, 3000 + i) for i, n in enumerate(sizes)]
@@ -90,7 +90,7 @@ def er1m():
     return g, deco.graph_from(g)
 
 
-def test_config4_sparse_idi_mean_full(er1m):
+def test_er1m_sparse_idi_mean_full(er1m):
     g, G = er1m
     h = torch.zeros(g.n, device=DEV)
     deco.deco_idi_mean(G, 0.2, 5, 0, h)
@@ -98,7 +98,7 @@ def test_config4_sparse_idi_mean_full(er1m):
     np.testing.assert_array_equal(h.cpu().numpy().astype(np.float64), O.idi_mean(g, 5, 0))
 
 
-def test_config4_sparse_step_and_cuts(er1m):
+def test_er1m_sparse_step_and_cuts(er1m):
     g, G = er1m
     C = 128
     sel, _ = deco.deco_autotune(G, C, deco.DECO_PREC_BF16, MUL, 0.0, 5)
@@ -132,7 +132,7 @@ def test_config4_sparse_step_and_cuts(er1m):
 
 
 @pytest.mark.parametrize("which", ["ba2000", "er5000"])
-def test_config5_proposal_full(which):
+def test_learned_eval_graphs_proposal_full(which):
     g = gg.ba_graph(2000, 4, 9001) if which == "ba2000" else gg.er_graph(5000, 0.002, 9002)
     m = deco.Mpnn(64, 3, 77)
     h = torch.zeros(g.n, device=DEV)

@@ -294,7 +294,7 @@ def _agreement(a, b):
     return float(np.mean(np.asarray(a) == np.asarray(b)))
 
 
-def test_solve_pquco_config1_explicit():
+def test_solve_pquco_er100_b64_explicit():
     # ER(100, 0.1) seed 0, B = 64, x0 ~ U[0,1], T = 500, alpha = 0.01, plain PGA
     g = gg.er_graph(100, 0.1, 0)
     B, T = 64, 500
