@@ -288,7 +288,7 @@ int deco_round_cut(const deco_graph* g, int32_t B, int32_t lift, int32_t ld, int
  *  x0       device, n x ld floats (DECO_INIT_EXPLICIT) or NULL.
  *  y        device, n x ld output block in `precision`.
  * Random draws: Philox4x32-10 with key = seed and counter
- * (row, column, phase, stream); see DESIGN notes in the source. */
+ * (row, column, phase, stream); Salmon et al., SC'11. */
 typedef struct deco_params {
   int32_t objective;          /* DECO_OBJ_* */
   int32_t precision;          /* DECO_PREC_* storage of the iterate */
