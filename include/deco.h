@@ -134,6 +134,12 @@ typedef enum deco_status {
  * (also by a single CTA), so that a cluster half as large fits.  Same
  * iterates as the other forms. */
 #define DECO_KERNEL_LEAN (1 << 20)
+/* With DECO_KERNEL_ONCHIP, the row-pair form: each half of a warp works on its
+ * own row (every lane on 8 bytes of the 128-byte replica row), so a warp
+ * advances two rows at a time and one shared load serves an entry of each.
+ * Same iterates as the other forms.  DECO_KERNEL_AUTO without a recorded
+ * tuning, and the batched on-chip launch of deco_solve_batch, use this form. */
+#define DECO_KERNEL_ROW_PAIRS (1 << 21)
 
 /* deco_create_graph flags */
 #define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */

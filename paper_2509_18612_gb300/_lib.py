@@ -48,6 +48,7 @@ DECO_KERNEL_ONCHIP = 2
 DECO_KERNEL_DENSE = 3
 DECO_KERNEL_DENSE_PER_STEP = 1 << 12
 DECO_KERNEL_LEAN = 1 << 20
+DECO_KERNEL_ROW_PAIRS = 1 << 21
 
 # every function include/deco.h declares (checked by the CPU test-suite)
 EXPORTED = [

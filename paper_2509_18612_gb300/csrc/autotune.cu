@@ -58,6 +58,9 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
   // the lean on-chip form (momentum in global memory, no staging area): a
   // cluster half as large fits, e.g. one wave instead of two
   for (int k = 1; k <= 8; k *= 2) cands.push_back(DECO_KERNEL_ONCHIP | (k << 8) | (2 << 12) | (2 << 14) | DECO_KERNEL_LEAN);
+  // every on-chip shape also in the row-pair form (a half-warp per row)
+  for (size_t i = 0, n0 = cands.size(); i < n0; ++i)
+    if ((cands[i] & 0xFF) == DECO_KERNEL_ONCHIP) cands.push_back(cands[i] | DECO_KERNEL_ROW_PAIRS);
   // dense tensor-core kernel: BF16 blocks of graphs with at least n^2 / 64 entries
   if (precision == DECO_PREC_BF16 && (double)g->nnz * 64.0 >= (double)g->n * (double)g->n)
     for (int k = 1; k <= 8; k *= 2) cands.push_back(DECO_KERNEL_DENSE | (k << 8));

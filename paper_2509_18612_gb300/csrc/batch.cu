@@ -578,6 +578,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
           sp.threads = 1024;
           sp.xmode = L->S.lean ? 2 : 0;
           sp.lean = L->S.lean ? 1 : 0;
+          sp.pairs = 1;   // row-pair form (256 BA graphs, FP32: 2.17 -> 1.83 s, same iterates)
           sp.steps = tmax;
           const float fac = p->objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
           sp.alpha = 0.0f;

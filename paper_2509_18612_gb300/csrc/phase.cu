@@ -65,8 +65,10 @@ bool valid_selector(int kernel) {
   const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
   const int s = (kernel >> 16) & 0xF;
   const int lean = (kernel >> 20) & 1;
-  if (kernel & ~0x1FFFFF) return false;
+  const int pairs = (kernel >> 21) & 1;
+  if (kernel & ~0x3FFFFF) return false;
   if (lean && kind != DECO_KERNEL_ONCHIP) return false;
+  if (pairs && kind != DECO_KERNEL_ONCHIP) return false;
   if (lean && x == 1) return false;   // the lean form exchanges through L2
   if (kind < DECO_KERNEL_AUTO || kind > DECO_KERNEL_DENSE || t == 3 || x == 3) return false;
   if (x && kind != DECO_KERNEL_ONCHIP) return false;
@@ -155,6 +157,9 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_x = (force >> 14) & 0x3;
   const int want_s = (force >> 16) & 0xF;
   const bool want_lean = ((force >> 20) & 1) != 0;
+  // the row-pair form is also the cost model's choice (measured faster on
+  // every on-chip shape of the benchmark); the autotuner times both forms
+  const bool want_pairs = ((force >> 21) & 1) != 0 || (force & 0xFF) == DECO_KERNEL_AUTO;
   force &= 0xFF;
   if (force == DECO_KERNEL_DENSE) {
     // BF16 blocks only; an FP32 block (e.g. the FP32 polish) is planned as AUTO
@@ -164,6 +169,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   plan->threads = want_t == 1 ? 512 : 1024;
   plan->xmode = want_x == 1 ? 1 : 2;   // DSMEM broadcast or L2 exchange (default)
   plan->lean = want_lean;
+  plan->pairs = want_pairs;
   if (force == DECO_KERNEL_GLOBAL) {
     if (want_s) {
       // column slabs of width w, run one after another in a slab-major copy
@@ -295,6 +301,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     p.threads = plan.threads;
     p.xmode = plan.lean ? 2 : plan.xmode;
     p.lean = plan.lean ? 1 : 0;
+    p.pairs = plan.pairs ? 1 : 0;
     p.steps = steps;
     const float fac = objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
     p.alpha = fac * alpha;

@@ -16,6 +16,7 @@ struct PhasePlan {
   int threads = 1024;            // CTA size of the on-chip kernel
   int xmode = 2;                 // exchange between cluster CTAs: 1 DSMEM, 2 L2
   bool lean = false;             // on-chip kernel: no staging area, momentum in global memory (L2 exchange)
+  bool pairs = false;            // on-chip kernel: row-pair form (a half-warp per row)
   int col_slabs = 1;             // global kernel: column slabs run one after another (slab-major)
   int slab_w = 0;                // their width
   int items = 0;                 // column slabs

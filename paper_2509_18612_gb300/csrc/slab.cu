@@ -148,6 +148,55 @@ __device__ __forceinline__ void gather_bf16(const unsigned char* lb, const uint3
 #undef DECO_ACC2
 }
 
+// Row-pair form: lanes 0-15 and 16-31 of a warp each work on their own row,
+// every lane on 8 bytes of the 128-byte replica row (2 FP32 or 4 BF16
+// columns), so one shared load serves one entry of each of the two rows.  Per
+// column the sums are the same as in gather_f32 / gather_bf16: the same
+// operation per entry, in list order.
+template <int SIGN, bool GEN, int PREC>
+__device__ __forceinline__ void gather_pair(const unsigned char* lb, const uint32_t* p, const float* w, int cnt,
+                                            float* acc) {
+#define DECO_ACCP(q, wv)                                                            \
+  {                                                                                 \
+    const uint2 u_ = *reinterpret_cast<const uint2*>(lb + (q));                     \
+    float v_[4];                                                                    \
+    if (PREC == DECO_PREC_FP32) {                                                   \
+      v_[0] = __uint_as_float(u_.x); v_[1] = __uint_as_float(u_.y);                 \
+    } else {                                                                        \
+      v_[0] = bf16lo(u_.x); v_[1] = bf16hi(u_.x); v_[2] = bf16lo(u_.y); v_[3] = bf16hi(u_.y); \
+    }                                                                               \
+    _Pragma("unroll") for (int c_ = 0; c_ < (PREC == DECO_PREC_FP32 ? 2 : 4); ++c_) \
+      acc[c_] = GEN ? fmaf((wv), v_[c_], acc[c_]) : (SIGN > 0 ? acc[c_] + v_[c_] : acc[c_] - v_[c_]); \
+  }
+#pragma unroll 1
+  for (; cnt >= 8; cnt -= 8, p += 8, w += 8) {
+    const uint4 q0 = *reinterpret_cast<const uint4*>(p);
+    const uint4 q1 = *reinterpret_cast<const uint4*>(p + 4);
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
+    if (GEN) { w0 = *reinterpret_cast<const float4*>(w); w1 = *reinterpret_cast<const float4*>(w + 4); }
+    DECO_ACCP(q0.x, w0.x) DECO_ACCP(q0.y, w0.y) DECO_ACCP(q0.z, w0.z) DECO_ACCP(q0.w, w0.w)
+    DECO_ACCP(q1.x, w1.x) DECO_ACCP(q1.y, w1.y) DECO_ACCP(q1.z, w1.z) DECO_ACCP(q1.w, w1.w)
+  }
+  if (cnt > 0) {
+    const uint4 q0 = *reinterpret_cast<const uint4*>(p);
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (GEN) w0 = *reinterpret_cast<const float4*>(w);
+    DECO_ACCP(q0.x, w0.x)
+    if (cnt > 1) DECO_ACCP(q0.y, w0.y)
+    if (cnt > 2) DECO_ACCP(q0.z, w0.z)
+    if (cnt > 3) DECO_ACCP(q0.w, w0.w)
+    if (cnt > 4) {
+      const uint4 q1 = *reinterpret_cast<const uint4*>(p + 4);
+      float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (GEN) w1 = *reinterpret_cast<const float4*>(w + 4);
+      DECO_ACCP(q1.x, w1.x)
+      if (cnt > 5) DECO_ACCP(q1.y, w1.y)
+      if (cnt > 6) DECO_ACCP(q1.z, w1.z)
+    }
+  }
+#undef DECO_ACCP
+}
+
 // ---- exchange helpers (inline PTX: mbarrier, bulk async copy, proxy fences)
 enum { XCHG_LOCAL = 0, XCHG_DSMEM = 1, XCHG_L2 = 2 };
 constexpr uint32_t XCHG_CHUNK = 32768;
@@ -205,7 +254,7 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int PREC, int WMODE, int NT, bool LEAN>
+template <int PREC, int WMODE, int NT, bool LEAN, bool PAIR>
 __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_xbar;
@@ -250,13 +299,18 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
     }
   }
 
-  // ---- per-lane column parameters
-  float alpha[2];
-  int32_t tmax[2];
+  // ---- per-lane column parameters: CPL columns from slab column cl0 (the
+  // row-pair form: half-warp hw, lane hl of it)
+  constexpr int CPL = PAIR ? (PREC == DECO_PREC_BF16 ? 4 : 2) : (PREC == DECO_PREC_BF16 ? 2 : 1);
+  const int hl = PAIR ? (lane & 15) : lane;
+  const int hw = PAIR ? (lane >> 4) : 0;
+  const int cl0 = hl * CPL;
+  float alpha[4];
+  int32_t tmax[4];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int c = col0 + (PREC == DECO_PREC_BF16 ? 2 * lane + h : lane);
-    const bool valid = (PREC == DECO_PREC_BF16 || h == 0) && c < C;
+  for (int h = 0; h < 4; ++h) {
+    const int c = col0 + cl0 + h;
+    const bool valid = h < CPL && c < C;
     alpha[h] = valid ? (G.alpha_cols ? P.afac * __ldg(G.alpha_cols + c) : P.alpha) : 0.0f;
     tmax[h] = valid ? (G.steps_cols ? __ldg(G.steps_cols + c) : P.steps) : 0;
   }
@@ -272,7 +326,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   const int wr0 = cost_search(rinfo, own, total * warp / (NT / 32));
   const int wr1 = cost_search(rinfo, own, total * (warp + 1) / (NT / 32));
 
-  const unsigned char* lb = smem + L.rep + lane * 4;   // this lane's word of replica row 0
+  const unsigned char* lb = smem + L.rep + (PAIR ? hl * 8 : lane * 4);   // this lane's bytes of replica row 0
   const bool lap = P.objective == DECO_OBJ_LAPLACIAN;
   const bool mom = P.mu != 0.0f;
   bool bad = false, timed_out = false;
@@ -292,6 +346,55 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   cluster.sync();   // every replica is loaded (and the barrier initialised) before any exchange
 
   for (int t = 0; t < P.steps; ++t) {
+    if constexpr (PAIR) {
+      // two rows per warp, one per half-warp (the second half idles on the
+      // last row of an odd range)
+      for (int rb = wr0; rb < wr1; rb += 2) {
+        const int rl = rb + hw;
+        const bool has = rl < wr1;
+        const int4 ri = has ? rinfo[rl] : make_int4(0, 0, 0, 0);
+        const int r = r0 + rl;
+        float vg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (LEAN && mom && has) {
+          const float* vrow = G.v + (size_t)r * ld + col0 + cl0;
+#pragma unroll
+          for (int h = 0; h < CPL; ++h) vg[h] = vrow[h];
+        }
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        gather_pair<+1, GEN, PREC>(lb, offs + ri.x, wts + ri.x, ri.y, acc);
+        if (WMODE == W_SIGN) gather_pair<-1, false, PREC>(lb, offs + ri.z, wts, ri.w, acc);
+        if (has) {
+          const uint2 wold = *reinterpret_cast<const uint2*>(smem + L.rep + (size_t)r * 128 + hl * 8);
+          float y[4];
+          if (PREC == DECO_PREC_FP32) {
+            y[0] = __uint_as_float(wold.x); y[1] = __uint_as_float(wold.y); y[2] = 0.0f; y[3] = 0.0f;
+          } else {
+            y[0] = bf16lo(wold.x); y[1] = bf16hi(wold.x); y[2] = bf16lo(wold.y); y[3] = bf16hi(wold.y);
+          }
+          const float dr = lap ? dn[rl] : 0.0f;
+          float out[4];
+#pragma unroll
+          for (int h = 0; h < CPL; ++h) {
+            const float grad = lap ? fmaf(dr, y[h], -acc[h]) : -acc[h];
+            float step = grad;
+            float* vp = LEAN ? G.v + (size_t)r * ld + col0 + cl0 + h : vsm + (size_t)rl * COLS + cl0 + h;
+            if (mom) step = fmaf(P.mu, LEAN ? vg[h] : *vp, grad);
+            const bool active = t < tmax[h];
+            float yn = fmaf(alpha[h], step, y[h]);
+            if (active && !isfinite(yn)) bad = true;
+            yn = fminf(fmaxf(yn, -1.0f), 1.0f);
+            out[h] = active ? yn : y[h];
+            if (mom && active) *vp = step;
+          }
+          uint2 word;
+          if (PREC == DECO_PREC_FP32) word = make_uint2(__float_as_uint(out[0]), __float_as_uint(out[1]));
+          else word = make_uint2(pack_bf16x2(out[0], out[1]), pack_bf16x2(out[2], out[3]));
+          unsigned char* dst = xmode == XCHG_L2 ? xnext + (size_t)r * 128
+                                                : reinterpret_cast<unsigned char*>(stage) + (size_t)rl * 128;
+          *reinterpret_cast<uint2*>(dst + hl * 8) = word;
+        }
+      }
+    } else {
     for (int rl = wr0; rl < wr1; ++rl) {
       const int4 ri = rinfo[rl];
       // LEAN: the row's momentum comes from global memory; its load is issued
@@ -335,6 +438,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
       const uint32_t word = PREC == DECO_PREC_FP32 ? __float_as_uint(out[0]) : pack_bf16x2(out[0], out[1]);
       if (xmode == XCHG_L2) reinterpret_cast<uint32_t*>(xnext)[(size_t)r * 32 + lane] = word;
       else stage[rl * 32 + lane] = word;
+    }
     }
     if (xmode == XCHG_L2) {
       // publish the own rows through L2, then refresh the whole replica with
@@ -387,7 +491,7 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
 
 template <int PREC, int WMODE, int NT, bool LEAN>
 cudaError_t launch_t(const SlabParams& p, int n_items, size_t smem, cudaStream_t st) {
-  auto fn = k_slab<PREC, WMODE, NT, LEAN>;
+  auto fn = p.pairs ? k_slab<PREC, WMODE, NT, LEAN, true> : k_slab<PREC, WMODE, NT, LEAN, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};

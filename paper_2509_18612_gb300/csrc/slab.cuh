@@ -47,6 +47,7 @@ struct SlabParams {
   int32_t load_v, store_v;
   int32_t max_n, max_own, max_img_words;
   int32_t lean;                // no staging area, momentum in global memory (needs xmode 2 and load_v)
+  int32_t pairs;               // row-pair form: a half-warp per row, two rows per warp
   int32_t* flag;
 };
 

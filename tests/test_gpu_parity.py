@@ -442,8 +442,10 @@ def _run_phase(g, y, v, C, ld, steps, objective, precision, alpha, mu, kernel, a
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
 @pytest.mark.parametrize("k,xchg", [(0, 0), (1, 0), (2, 0), (4, 0), (8, 0), (2, 1), (4, 1), (8, 1),
                                     (1, 4), (2, 4), (4, 4)])
-def test_onchip_phase_bitwise_equals_global(name, precision, k, xchg):
-    # xchg 4: the lean form (momentum in global memory, rows through L2)
+@pytest.mark.parametrize("pairs", [False, True])
+def test_onchip_phase_bitwise_equals_global(name, precision, k, xchg, pairs):
+    # xchg 4: the lean form (momentum in global memory, rows through L2);
+    # pairs: the row-pair form (a half-warp per row)
     g = GRAPHS[name]()
     cols = 64 if precision == deco.DECO_PREC_BF16 else 32
     C = 3 * cols - 5                                # three slabs, ragged last slab
@@ -458,6 +460,8 @@ def test_onchip_phase_bitwise_equals_global(name, precision, k, xchg):
     sel = deco.DECO_KERNEL_ONCHIP | (k << 8) | ((xchg & 3) << 14)   # xchg 1: DSMEM broadcast, 0: L2 (default)
     if xchg == 4:
         sel |= deco.DECO_KERNEL_LEAN
+    if pairs:
+        sel |= deco.DECO_KERNEL_ROW_PAIRS
     try:
         got_y, got_v, f1 = _run_phase(g, y, v, C, ld, 9, objective, precision, 0.0, mu, sel, alpha_cols, steps_cols)
     except deco.DecoError as e:
@@ -594,9 +598,9 @@ def test_batch_kernels_and_replay_agree():
 @pytest.mark.parametrize("sizes", [(150, 300), (300, 1150)])
 def test_batch_onchip_items_equal_the_union_per_step_kernel(precision, sizes):
     # 40 graphs whose union does not fit in shared memory while every member
-    # does: the default runs one on-chip launch with an item per (graph,
-    # 128-byte column slab) -- with graphs of up to 1 150 rows in the lean
-    # form (momentum in global memory, replica refreshed from L2); the
+    # does: the default runs one on-chip launch (row-pair form) with an item
+    # per (graph, 128-byte column slab) -- with graphs of up to 1 150 rows in
+    # the lean form (momentum in global memory, replica refreshed from L2); the
     # per-step kernel over the union performs the same FP32 operations in the
     # same order
     rng = np.random.default_rng(77)
