@@ -20,6 +20,10 @@
 // every neighbour as the byte offset of its replica row, in 16-byte aligned
 // per-row lists, so one edge costs one 16-byte broadcast index load per four
 // edges, one address add, one shared load and one add.
+// Row-pair form: the two halves of a warp work on two rows at once, every
+// lane on 8 bytes of the replica row, so one shared load instruction covers
+// an entry of each row and a warp walks half as many per-row chains (the
+// same wavefronts per edge, the same sums per column).
 #include <cooperative_groups.h>
 
 #include <algorithm>
