@@ -213,8 +213,8 @@ typedef struct deco_step_args {
 int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void* y_out,
               float* v, const deco_step_args* a, int32_t* nonfinite_flag, void* stream);
 
-/* `steps` projected gradient ascent steps in place (Alg. 1 / Alg. 2 lines
- * 2-3): y holds the starting block and receives the result.
+/* `steps` projected gradient ascent steps in place (the step loop of Alg. 1 /
+ * Alg. 2): y holds the starting block and receives the result.
  *  C, ld   as in deco_step; the on-chip kernel needs ld % 32 == 0 (FP32) or
  *          ld % 64 == 0 (BF16) and treats columns in [C, ld) as inactive.
  *  v       device n x ld float momentum, read at the start and written at the
@@ -275,7 +275,8 @@ int deco_set_tuning(const deco_graph* g, int32_t C, int32_t precision, int32_t k
 int deco_run_phase_noalloc(const deco_graph* g, int32_t C, int32_t ld, void* y, float* v, int32_t steps,
                            const deco_step_args* a, int32_t* nonfinite_flag, void* stream);
 
-/* Rounding + cut + argmax of a block (Alg. 1/2 lines 4-6).
+/* Rounding + cut + argmax of a block (the rounding and selection steps of
+ * Alg. 1 / Alg. 2).
  *  B, lift  starting points and lift l (C = B*l columns in y, ld >= C).
  *  y        device, n x ld, precision `precision`.
  *  zbits    device, n x ceil(B/32) uint32 (bit b%32 of word b/32 = z_{v,b}):
@@ -378,8 +379,8 @@ int deco_solve(const deco_graph* g, int32_t B, const deco_phase* phases, int32_t
                const deco_params* p, uint64_t seed, const float* x0, const float* mean,
                uint8_t* assignment, int64_t* phase_cuts, void* stream, deco_result* out);
 
-/* pDECO under a time budget (Alg. 3: the schedule is repeated until the
- * time budget expires), resumable.  Repetition r runs deco_solve with seed
+/* pDECO under a time budget (Alg. 3: the schedule is repeated while the
+ * budget lasts), resumable.  Repetition r runs deco_solve with seed
  * + r; repetition 0 starts as p->init says, or, when `warm` is given, from
  * Gaussian starts around 2 warm - 1; every later repetition starts around
  * 2 z* - 1 of the best vector found so far (DECO_INIT_MEAN, Sec. 4.2).  The

@@ -190,7 +190,7 @@ def pga_step(g, Y, alpha, objective=OBJ_MULTILINEAR01, V=None, momentum=0.0,
 
 
 # ----------------------------------------------------------------------------
-# Binarisation (Eq. 5 / Eq. 11), best-of-batch (Alg. 1-2 lines 4-6)
+# Binarisation (Eq. 5 / Eq. 11), best of the batch (the rounding and selection steps of Alg. 1 and Alg. 2)
 # ----------------------------------------------------------------------------
 
 def binarize(Y, lift: int = 1) -> np.ndarray:
@@ -213,7 +213,7 @@ def binarize(Y, lift: int = 1) -> np.ndarray:
 
 
 def best_of(cuts) -> int:
-    """argmax over inits, lowest index on ties (Alg. 1 line 6; reading for ties)."""
+    """argmax over inits, lowest index on ties (the selection step of Alg. 1; reading for ties)."""
     cuts = np.asarray(cuts)
     return int(np.flatnonzero(cuts == cuts.max())[0])
 
@@ -363,8 +363,9 @@ def gaussian_block(mean, C: int, seed: int, phase: int, eta: float, scale: float
                    col_offset: int = 0) -> np.ndarray:
     """Y[v,c] = Proj[-1,1]( s * (h_v + sqrt(eta) * N(0,1)) ) (Sec. 4.2, Sec. 5).
 
-    Reading: "scale the initial vectors down" applies to the whole Gaussian
-    draw (mean plus noise); the projection keeps the result in the box.
+    Reading: the down-scaling of the initial vectors (Sec. 5) applies to the
+    whole Gaussian draw (mean plus noise); the projection keeps the result in
+    the box.
     Noise for column c uses counter (v, c + col_offset, phase, STREAM_INIT).
     eta and scale are given as FP32 values and widened to FP64.
     """
@@ -457,7 +458,7 @@ def initial_block(g, B: int, lift: int, params: Params, seed: int, x0=None, phas
 
 
 def run_phase(g, Y, phase: Phase, objective: str, alpha_cols=None, active_steps=None):
-    """T_k projected gradient steps on the whole block (Alg. 1/2 lines 1-3)."""
+    """T_k projected gradient steps on the whole block (the step loop of Alg. 1 / Alg. 2)."""
     A = adjacency(g)
     d = net_degree(g)
     V = np.zeros_like(Y)
@@ -526,8 +527,8 @@ def solve(g, B: int, phases: Sequence[Phase], params: Params, seed: int, x0=None
 
 
 def solve_repeated(g, B: int, phases: Sequence[Phase], params: Params, seed: int, repeats: int, warm=None):
-    """pDECO repeated ``repeats`` times (Alg. 3 repeats its schedule until the
-    time budget expires; here the budget is a number of repetitions).
+    """pDECO repeated ``repeats`` times (Alg. 3 repeats its schedule while its
+    time budget lasts; here the budget is a number of repetitions).
     Repetition r solves with seed + r; it starts as ``params.init`` says, or
     around 2 z* - 1 (init "mean") once a best vector z* exists (the warm
     start, or an earlier repetition's best).  Returns (best cut, best z)."""

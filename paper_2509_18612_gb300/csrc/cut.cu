@@ -1,5 +1,5 @@
 // Rounding, integer cut evaluation and argmax over starting points
-// (Alg. 1 / Alg. 2 lines 4-6; Eq. 5, Eq. 11, Eq. 1).
+// (the rounding and selection steps of Alg. 1 / Alg. 2; Eq. 5, Eq. 11, Eq. 1).
 //
 //  pack:   one warp per (row, 32 starting points); lane b forms z_{v,b} from
 //          the iterate and __ballot_sync packs the 32 bits into one word.

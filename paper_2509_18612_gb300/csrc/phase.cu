@@ -1,4 +1,4 @@
-// One phase of projected gradient ascent (Alg. 1 / Alg. 2 lines 2-3): T steps
+// One phase of projected gradient ascent (the step loop of Alg. 1 / Alg. 2): T steps
 // on a device block, by the persistent on-chip kernel (slab.cu) when one
 // column slab of the graph fits in shared memory, otherwise by one launch of
 // the global-memory kernel (step_global.cu) per step.

@@ -1,5 +1,5 @@
 // Persistent on-chip PGA kernel for graphs whose iterate slab fits in shared
-// memory: all T steps of one phase (Alg. 1 / Alg. 2 lines 2-3) run inside one
+// memory: all T steps of one phase (the step loop of Alg. 1 / Alg. 2) run inside one
 // launch, with no trip through global memory between steps.
 //
 // Work unit ("item") = (graph, column slab).  A slab is 128 bytes of every row:
