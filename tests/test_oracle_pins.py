@@ -635,3 +635,101 @@ def test_fresh_later_phases_do_not_depend_on_earlier_ones():
     with pytest.raises(ValueError):
         O.solve(g, 4, [O.Phase(1, 3, 0.01, 0.0), O.Phase(1, 3, 0.01, 0.0)],
                 O.Params(init="explicit", phase_init="fresh"), 0, x0=gg.uniform_x0(g.n, 4, 0))
+
+
+# ------------------------------------------------- starts of later phases
+
+def _random_signs_graph():
+    # unit-weight ER graph whose phase-0 starts (uniform signs) give distinct cuts
+    return gg.er_graph(40, 0.2, 21)
+
+
+@pytest.mark.parametrize("objective", [O.OBJ_MULTILINEAR01, O.OBJ_LAPLACIAN])
+def test_later_phase_starts_at_the_best_vector_mapped_to_plus_minus_one(objective):
+    # Sec. 4.2: a later batch is drawn around the previous batch's best binary
+    # vector z*, mapped to the box's vertex 2 z* - 1.  With eta = 0 the draw is
+    # the centre itself, scaled by s, so the next phase's start (0 steps) is
+    # exactly s (2 z* - 1).  Centring on z* (0/1), on another start's vector or
+    # on a negated vector fails here.
+    g = _random_signs_graph()
+    s = 0.25
+    p = O.Params(objective=objective, init="uniform", uniform_half_width=1.0, eta=0.0, scale=s)
+    res = O.solve(g, 16, [O.Phase(1, 0, 0.01), O.Phase(1, 0, 0.01)], p, 5, keep_final=True)
+    cuts0 = res.phase_cuts[0]
+    assert len(set(cuts0.tolist())) > 3            # the starts really differ
+    b = int(np.argmax(cuts0))                       # lowest index among the best
+    Y0 = O.initial_block(g, 16, 1, p, 5)
+    z = (Y0[:, b] > 0).astype(np.float64)           # Eq. 5 of the best start
+    expect = float(np.float32(s)) * (2.0 * z - 1.0)
+    assert np.array_equal(res.final_Y, np.repeat(expect[:, None], 16, axis=1))
+
+
+def test_later_lifted_phase_rounds_every_start_to_the_previous_best():
+    # The same centre seen through Eq. 11: a lifted start s (2 z* - 1) in both
+    # components rounds to z* in every start (row sums -2s < 0 or 2s >= 0), so
+    # every start of the lifted phase cuts exactly the previous best cut.  A
+    # 0/1 centre would give zero rows, which Eq. 11's >= 0 rounds to 1 (cut 0).
+    g = _random_signs_graph()
+    p = O.Params(init="uniform", uniform_half_width=1.0, eta=0.0, scale=1e-4)
+    res = O.solve(g, 12, [O.Phase(1, 0, 0.01), O.Phase(2, 0, 0.01)], p, 9)
+    assert np.all(res.phase_cuts[1] == res.phase_cuts[0].max())
+
+
+def test_batch_search_later_round_rounds_every_start_to_each_graphs_best():
+    # Sec. 4.2 inside the batched search (Sec. 4.3): round r > 0 of graph i is
+    # drawn around 2 z_i* - 1, z_i* that graph's best vector of round r - 1.
+    # With zero steps (T_l = T_u = 0) and eta = 0, a lifted round 1 rounds
+    # every start of graph i to z_i*, so every cut equals graph i's round-0
+    # best.  A 0/1 centre (cut 0), the worst start's vector or another graph's
+    # vector fails.
+    graphs = [gg.er_graph(n, 0.2, 30 + n) for n in (24, 31, 40)]
+    p = O.Params(init="uniform", uniform_half_width=1.0, eta=0.0)
+    res = O.solve_batch_population(graphs, 8, 4, 2, [1, 2], 0, 0, -3.0, -1.0, 0.0, p, 4)
+    r0, r1 = res.round_cuts
+    for gi in range(len(graphs)):
+        assert len(set(r0[gi].tolist())) > 2
+        assert np.all(r1[gi] == r0[gi].max())
+
+
+def test_uniform_block_is_an_affine_map_of_the_uniform_draws():
+    # y = h (2u - 1): the values fill (-h, h) uniformly (a map onto [0, h], a
+    # missing factor 2 or h, or a shift fails the range or the KS test), and
+    # column c of a block with a column offset k is column c + k of the plain
+    # block (the counter's column is the global column index).
+    stats = pytest.importorskip("scipy.stats")
+    h = 0.375
+    Y = O.uniform_block(300, 64, 17, 0, h)
+    assert Y.min() > -h and Y.max() < h
+    assert Y.min() < -0.99 * h and Y.max() > 0.99 * h
+    assert stats.kstest(Y.ravel(), "uniform", args=(-h, 2 * h)).pvalue > 1e-4
+    assert abs(Y.mean()) < 0.01 * h
+    np.testing.assert_array_equal(O.uniform_block(300, 40, 17, 0, h, col_offset=24), Y[:, 24:])
+    # two rows of the draw, written out: u from the pinned generator's u01 map
+    u = O.draw_uniform(np.array([[3]], dtype=np.uint64), np.array([[5]], dtype=np.uint64), 0, O.STREAM_INIT, 17)
+    assert Y[3, 5] == float(np.float32(h)) * (2.0 * float(u[0, 0]) - 1.0)
+
+
+@pytest.mark.parametrize("lift", [1, 2])
+def test_idi_plus_uniform_split_of_the_starts(lift):
+    # Reading of the "IDI + random" starts: starting points [0, B/2) are
+    # Gaussian around s h_IDI, starting points [B/2, B) uniform s (2u - 1);
+    # with lift l a starting point owns l adjacent columns.
+    stats = pytest.importorskip("scipy.stats")
+    g = gg.er_graph(120, 0.08, 6)
+    B, s = 40, 1e-3
+    h = O.idi_mean(g, 8, 0, 0.2)
+    half = (B // 2) * lift
+    # eta = 0: the IDI half is exactly s h (|y| = s), the uniform half lies
+    # strictly inside (-s, s) and fills it
+    Y = O.initial_block(g, B, lift, O.Params(init="idi_half_uniform", eta=0.0, scale=s), 8)
+    assert Y.shape == (g.n, B * lift)
+    sf = float(np.float32(s))
+    assert np.array_equal(Y[:, :half], np.repeat((sf * h)[:, None], half, axis=1))
+    U = Y[:, half:]
+    assert np.all(np.abs(U) < sf)
+    assert stats.kstest(U.ravel(), "uniform", args=(-sf, 2 * sf)).pvalue > 1e-4
+    # eta = 0.8: the IDI half's row means track s h, the uniform half's track 0
+    Y = O.initial_block(g, 2000, lift, O.Params(init="idi_half_uniform", eta=0.8, scale=s), 8)
+    half = 1000 * lift
+    np.testing.assert_allclose(Y[:, :half].mean(axis=1), sf * h, atol=0.15 * sf)
+    np.testing.assert_allclose(Y[:, half:].mean(axis=1), 0.0, atol=0.15 * sf)
