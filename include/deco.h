@@ -268,6 +268,9 @@ int deco_set_tuning(const deco_graph* g, int32_t C, int32_t precision, int32_t k
  *  No cudaMalloc, cudaFree or other allocating call is made.
  *  The first call on a device looks up the array's device address
  *  (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  The address is kept with the unique id of the CUDA context it belongs to;
+ *  the first call after the context was torn down and re-created (e.g. by
+ *  cudaDeviceReset) looks it up again, so it too must come before a capture.
  *  All calls share the one array: calls whose work overlaps on the GPU (other
  *  streams, other host threads) race on it and must be serialised by the
  *  caller.  Nothing in the array needs to start at zero.
@@ -572,6 +575,16 @@ int deco_probe_wait_timeout(int32_t which, float* waited_ms, void* stream);
  * CUDA context usable.  k = 0 disarms it.  Process-wide, not thread-safe
  * against concurrent calls.  No paper counterpart.  Errors: DECO_ERR_ARG. */
 int deco_debug_fail_scratch_alloc(int32_t k);
+
+/* Diagnostic for tests of allocation behaviour: the current device's current
+ * stream-ordered memory pool, from which every scratch buffer of the library
+ * is taken (cudaMallocAsync).  used_now (host, or NULL) receives the bytes of
+ * the pool in use now, used_high (host, or NULL) the most bytes in use at once
+ * since the high-water mark was last reset; reset != 0 then restarts the
+ * high-water mark from the current use.  Process-wide (the pool is shared with
+ * every other user of it in the process).  No paper counterpart.
+ * Errors: CUDA. */
+int deco_debug_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset);
 
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* deco_last_error(void);

@@ -59,8 +59,8 @@ EXPORTED = [
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_solve_budget", "deco_greedy", "deco_local_search",
-    "deco_probe_mma_rate", "deco_probe_wait_timeout", "deco_debug_fail_scratch_alloc", "deco_last_error",
-    "deco_abi_version",
+    "deco_probe_mma_rate", "deco_probe_wait_timeout", "deco_debug_fail_scratch_alloc", "deco_debug_pool_usage",
+    "deco_last_error", "deco_abi_version",
 ]
 
 
@@ -146,6 +146,7 @@ def _load():
         "deco_probe_mma_rate": (ctypes.c_int, [I32, I32, I32, P, P]),
         "deco_probe_wait_timeout": (ctypes.c_int, [I32, P, P]),
         "deco_debug_fail_scratch_alloc": (ctypes.c_int, [I32]),
+        "deco_debug_pool_usage": (ctypes.c_int, [P, P, I32]),
         "deco_last_error": (ctypes.c_char_p, []),
         "deco_abi_version": (ctypes.c_int, []),
     }
@@ -347,6 +348,15 @@ def deco_probe_wait_timeout(which: int, stream=None):
 def deco_debug_fail_scratch_alloc(k: int):
     """Fail the k-th scratch allocation from now on with DECO_ERR_OOM (0 disarms)."""
     _check(lib.deco_debug_fail_scratch_alloc(int(k)))
+
+
+def deco_debug_pool_usage(reset: bool = False):
+    """(bytes in use, high-water mark) of the current device's stream-ordered
+    memory pool, which every scratch buffer of the library comes from; with
+    reset the high-water mark then restarts from the current use."""
+    now, high = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.deco_debug_pool_usage(ctypes.byref(now), ctypes.byref(high), 1 if reset else 0))
+    return int(now.value), int(high.value)
 
 
 def deco_set_tuning(g: Graph, C: int, precision: int, kernel: int):

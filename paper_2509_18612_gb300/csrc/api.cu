@@ -49,6 +49,24 @@ extern "C" int deco_debug_fail_scratch_alloc(int32_t k) {
   return DECO_OK;
 }
 
+extern "C" int deco_debug_pool_usage(int64_t* used_now, int64_t* used_high, int32_t reset) {
+  clear_error();
+  int dev = 0;
+  DECO_CUDA_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool = nullptr;
+  DECO_CUDA_TRY(cudaDeviceGetMemPool(&pool, dev));
+  cuuint64_t now = 0, high = 0;
+  DECO_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &now));
+  DECO_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+  if (used_now) *used_now = (int64_t)now;
+  if (used_high) *used_high = (int64_t)high;
+  if (reset) {
+    cuuint64_t zero = 0;   // the high-water mark restarts from the current use
+    DECO_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+  }
+  return DECO_OK;
+}
+
 extern "C" int deco_step(const deco_graph* g, int32_t C, int32_t ld, const void* y_in, void* y_out,
                          float* v, const deco_step_args* a, int32_t* nonfinite_flag, void* stream) {
   clear_error();

@@ -23,12 +23,58 @@ namespace {
 constexpr size_t kPhaseScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_phase_scratch[kPhaseScratchBytes];
 
-// Device address of g_phase_scratch, looked up once per device.  Host code
-// may not use the symbol itself as a device pointer: on the host it only
-// names a host-side stand-in.
+// Device address of g_phase_scratch, looked up once per (device, context).
+// Host code may not use the symbol itself as a device pointer: on the host it
+// only names a host-side stand-in.  The address belongs to the CUDA context
+// that loaded the module, so it is cached together with that context's
+// unique id (cuCtxGetId: never reused within a process): after a
+// cudaDeviceReset, or any other teardown and re-creation of the context, the
+// next call sees a new id and looks the address up again instead of handing
+// the kernel a stale pointer.
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;   // id of the context current when the address was taken
+  void* addr = nullptr;
+};
+ScratchSlot g_scratch_slot[kMaxDevices];
 std::mutex g_scratch_mutex;
+
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry-point
+// query, so that the library needs no link-time dependency on the driver API.
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+template <typename F>
+int driver_fn(const char* name, F* fn) {
+  if (*fn) return DECO_OK;
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  cudaError_t e = cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDriverEntryPointByVersion");
+  if (q != cudaDriverEntryPointSuccess || !f) {
+    set_error("%s is not available from the driver", name);
+    return DECO_ERR_CUDA;
+  }
+  *fn = reinterpret_cast<F>(f);
+  return DECO_OK;
+}
+
+// unique id of the current context (DECO_ERR_CUDA when none is current)
+int current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  int rc = driver_fn("cuCtxGetCurrent", &get_current);
+  if (rc || (rc = driver_fn("cuCtxGetId", &get_id))) return rc;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) {
+    set_error("no current CUDA context");
+    return DECO_ERR_CUDA;
+  }
+  if (get_id(ctx, id) != 0) {
+    set_error("cuCtxGetId failed");
+    return DECO_ERR_CUDA;
+  }
+  return DECO_OK;
+}
 
 int scratch_address(void** out) {
   int dev = 0;
@@ -38,14 +84,25 @@ int scratch_address(void** out) {
     set_error("device ordinal %d is beyond the %d devices this entry point tracks", dev, kMaxDevices);
     return DECO_ERR_UNSUPPORTED;
   }
+  // the context the kernels will run in; with none current yet, cudaSetDevice
+  // makes the device's primary context current (creating it on first use)
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long ctx_id = 0;
+  int rc = current_context_id(&ctx_id);
+  if (rc) {
+    clear_error();
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if ((rc = current_context_id(&ctx_id))) return rc;
+  }
+  ScratchSlot& slot = g_scratch_slot[dev];
+  if (!slot.addr || slot.ctx_id != ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_phase_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_phase_scratch)");
-    g_scratch_addr[dev] = p;
+    slot.addr = p;
+    slot.ctx_id = ctx_id;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return DECO_OK;
 }
 
