@@ -486,7 +486,8 @@ __device__ __forceinline__ bool grid_wait(const unsigned int* gbar, uint32_t tar
 template <bool MOM, bool LAP, int KS>
 __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ PhaseArgs args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[P_MAX_SB], empty[P_MAX_SB], emptyA[P_MAX_SA], done, recv_full, out_free;
+  __shared__ __align__(8) uint64_t full[P_MAX_SB], empty[P_MAX_SB], emptyA[P_MAX_SA], done, recv_full, out_free,
+      drain[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int sh_timeout;
   const DenseStep& p = args.p;
@@ -538,6 +539,8 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     mbar_init(&done, nloc > 1 ? 2 : 1);   // one commit per issuer with chunks
     mbar_init(&recv_full, 1);
     mbar_init(&out_free, 1);   // the update warps are done with `out` (ring memory) for the step
+    mbar_init(&drain[0], 1);   // give-up path: an MMA issuer's last commit
+    mbar_init(&drain[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh_timeout = 0;
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&args.tmA)) : "memory");
@@ -575,12 +578,19 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     // its round u - 1 have completed (phase (u - 1) & 1 of its empty barrier).
     int bslot = 0, bround = 0, aslot = 0, around = 0;
     int pre_slot[P_MAX_SB];
-    for (int t = 0; t < args.steps && !timed_out; ++t) {
+    // per B stage: round of the last phase of full[s] armed with expect_tx
+    // (-1: never), and the x coordinate of a B tile counted in that phase but
+    // not requested yet (-1: none) -- what the give-up path must complete
+    int last_round[P_MAX_SB], pend_x[P_MAX_SB];
+    for (int q = 0; q < P_MAX_SB; ++q) last_round[q] = pend_x[q] = -1;
+    int t = 0;
+    for (; t < args.steps && !timed_out; ++t) {
       const CUtensorMap* tmY = &args.tmY[t & 1];
       // the rings also hold `out` between steps: wait until the update of step t-1 is done with it
       if (t > 0 && !mbar_wait(&out_free, (uint32_t)(t - 1) & 1u)) { timed_out = true; break; }
       auto acquire = [&](int kc, int& bs) -> bool {   // the chunk's stages are free, its bytes expected
         bs = bslot;
+        const int rnd = bround;
         if (bround > 0 && !mbar_wait(&empty[bslot], (uint32_t)(bround - 1) & 1u)) return false;
         if (++bslot == SB) { bslot = 0; ++bround; }
         if (kc < kr) {
@@ -591,6 +601,8 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         } else {
           mbar_expect_tx(&full[bs], b_bytes);
         }
+        last_round[bs] = rnd;
+        pend_x[bs] = (kb + kc) * BK;
         return true;
       };
       // A tiles of the first streamed chunks: no dependence on the new iterate
@@ -608,7 +620,21 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         if (kc < pre) bs = pre_slot[kc];
         else if (!acquire(kc, bs)) { timed_out = true; break; }
         tma_load_2d(base + (uint32_t)bs * b_bytes, tmY, (kb + kc) * BK, cbase, &full[bs]);
+        pend_x[bs] = -1;
       }
+    }
+    if (timed_out) {
+      // Give-up path.  A stage armed for a B tile that was never requested
+      // (the wait for the grid barrier or a stage gave up in between) would
+      // never complete: request the tile now (an in-bounds read whose bytes
+      // are discarded).  Then wait for the last armed phase of every stage,
+      // so that no TMA write into this CTA's shared memory is in flight when
+      // the CTA releases it.
+      const int tl = t < args.steps ? t : args.steps - 1;
+      for (int q = 0; q < SB; ++q)
+        if (pend_x[q] >= 0) tma_load_2d(base + (uint32_t)q * b_bytes, &args.tmY[tl & 1], pend_x[q], cbase, &full[q]);
+      for (int q = 0; q < SB; ++q)
+        if (last_round[q] >= 0) (void)mbar_wait(&full[q], (uint32_t)last_round[q] & 1u);
     }
   } else if (tid == 32 || (tid == 64 && nloc > 1)) {
     // ---------------- MMA issuers (the same slot / round walk as the producer;
@@ -642,6 +668,12 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
         mma_commit(&empty[s]);
       }
       mma_commit(&done);   // phase t of `done` completes with both issuers' accumulators of step t
+    }
+    if (timed_out) {
+      // give-up path: every MMA this thread issued has completed (its writes
+      // to tensor memory and its reads of the stages) before the teardown
+      mma_commit(&drain[my]);
+      (void)mbar_wait(&drain[my], 0u);
     }
   } else if (warp >= 3) {
     // ---------------- update warps: et = row-vector owner index, quarter = TMEM lanes
@@ -777,21 +809,17 @@ __global__ void __launch_bounds__(PT, 1) k_dense_phase(const __grid_constant__ P
     }
     if (p.flag && bad) atomicOr(p.flag, 1);
   }
+  // The exchange's issuing thread waits until its bulk copies have been
+  // written into the peers (not only read here): once every CTA of the
+  // cluster has passed the cluster barrier below, no copy into any of them is
+  // in flight.  The producer and the MMA issuers drained their own loads and
+  // MMAs above on the give-up path, so tensor memory and shared memory are
+  // quiet when they are released.
+  if (tid == 96) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncwarp();
   if (timed_out) atomicOr(&sh_timeout, 1);
   __syncthreads();
-  if (sh_timeout) {
-    // a wait gave up: report it, and give this CTA's own loads and copies
-    // still in flight time to land (100 us, far above their latency)
-    if (tid == 0) {
-      if (p.flag) atomicOr(p.flag, 2);
-      const uint64_t t0 = gtimer();
-      while (gtimer() - t0 < 100000ull) {
-      }
-    }
-    if (tid == 96) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // the exchange's issuing thread
-    __syncthreads();
-  }
+  if (sh_timeout && tid == 0 && p.flag) atomicOr(p.flag, 2);
   tc_fence_before();
   cluster.sync();   // no peer copies into this CTA any more
   tc_fence_after();
@@ -1077,12 +1105,14 @@ int launch_dense_phase(const DenseStep& p, const DenseMaps& maps, __nv_bfloat16*
   attr[1].val.cooperative = 1;
   cfg.numAttrs = 2;
   e = cudaLaunchKernelEx(&cfg, fn, args);
-  if (e != cudaSuccess) {
-    // a driver that does not combine cooperative and cluster launches: the
-    // occupancy check above already guarantees residency
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported || e == cudaErrorNotPermitted) {
+    // The grid barrier needs every CTA resident at once, which only the
+    // cooperative launch guarantees (the occupancy figure above is a bound,
+    // not a promise on a GPU shared with other work): without it the caller
+    // runs the per-step kernel instead.
     cudaGetLastError();
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, fn, args);
+    set_error("dense phase kernel: the cooperative cluster launch was refused (%s)", cudaGetErrorString(e));
+    return DECO_ERR_UNSUPPORTED;
   }
   if (e != cudaSuccess) return cuda_fail(e, "dense phase launch");
   return DECO_OK;
