@@ -1,18 +1,24 @@
 """Benchmark of the DECO MaxCut hot path on one GB300 (or N replicas).
 
-Workload (one "step"): a full pDECO solve (Alg. 3) of two synthetic graphs,
-Erdos-Renyi G(800, 0.06) and a 40 x 20 torus with +-1 weights, each with
-B = 1024 starting points (512 IDI-centred Gaussian + 512 uniform), momentum
-0.9, schedule 2 x (800 unlifted steps alpha = 0.01 + 200 lifted steps l = 2
-alpha = 0.001), T = 2000; rounding, integer cuts and argmax after every phase.
+Headline workload (one "step"): a pQUCO solve (Alg. 1) of a synthetic
+Erdos-Renyi graph with n = 10^6 nodes and average degree 10 (about 10^7 stored
+CSR entries, seed 4): B = 128 IDI-centred starting points held in BF16 with
+FP32 accumulation, T = 1000 plain projected-gradient steps (alpha = 0.01),
+then rounding, integer cuts and the argmax over the starting points.  This is
+the largest configuration of the method on one GPU: its step is bound by HBM.
 
 Metric: edge-updates/s = sum over phases of nnz * B * l * steps / seconds.
+
+The other workloads (the ER(800) + torus pDECO of B = 1024, the dense
+ER(4096, 0.5) tensor-core path, the 256-graph population batch, the learned
+proposal, the greedy comparison, the lifting sweep and the initialisation
+ablation) are reported under "workloads".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl deco|reference]
 
 `--impl reference` times the CPU oracle (FP64, single thread) on a bounded
-sample of the same workload (the first phase, a slice of the starting
-points, a few steps) and reports the same metric.
+sample of the headline workload (one FP64 step of the whole 10^6 x 128 block
+per bench step) and reports the same metric.
 """
 from __future__ import annotations
 
@@ -34,6 +40,8 @@ if ROOT not in sys.path:
 import graphgen as gg  # noqa: E402
 
 METRIC = "edge-updates/s (nnz x inits x iters / s)"
+HEAD_WORKLOAD = ("ER(n=1e6, avg deg 10, seed 4); B=128 IDI starts, X bf16 with FP32 accumulation; "
+                 "pQUCO T=1000, alpha=0.01, plain PGA; rounding + integer cuts + argmax")
 WORKLOAD = "ER(n=800,p=0.06)+torus40x20(+-1); B=1024 (512 IDI + 512 uniform); pDECO T=2000 = 2x(800 unlifted a=0.01 + 200 lifted l=2 a=0.001), mu=0.9"
 B = 1024
 SCHEDULE = [(1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9), (1, 800, 0.01, 0.9), (2, 200, 0.001, 0.9)]
@@ -45,12 +53,15 @@ def graphs():
 
 ER1M_B = 128
 ER1M_STEPS = 1000
-# DRAM bytes (read + write) of one launch, from the ncu capture summarised in
-# profiles/: k_step_global on ER(1e6), 128 BF16 columns, plain schedule; and
-# k_slab on ER(800), 1024 FP32 columns, 800 steps, cluster 4 / 1024 threads / L2,
-# row-pair form (selector 0x20a402).
-K_STEP_ER1M_TRAFFIC = 2013752064 + 248812288
-K_SLAB_ER800_TRAFFIC = 6759680 + 0
+ER1M_ALPHA = 0.01
+# DRAM bytes (read + write) of one launch, from ncu captures of the kernels as
+# they are now, keyed by (kernel, launch-shape selector): the per-step kernel
+# on ER(1e6) with 128 BF16 columns, and the on-chip kernel on ER(800) with 1024
+# FP32 columns, 800 steps, cluster 4 / 1024 threads / L2 exchange, row pairs.
+# A kernel changed since its capture has no entry (traffic reported as null).
+DRAM_TRAFFIC = {
+    ("k_slab", 0x20a402): 6759680 + 0,
+}
 
 
 DENSE_N, DENSE_P, DENSE_B, DENSE_STEPS, DENSE_ALPHA = 4096, 0.5, 128, 1000, 1e-4
@@ -296,7 +307,8 @@ def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
     ach = gathered / t / 1e9
     sel = tuned_selector_hint
     return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
-            "traffic": K_SLAB_ER800_TRAFFIC if sel == "0x20a402" and args.precision == "fp32" else None,
+            "traffic": (DRAM_TRAFFIC.get(("k_slab", int(sel, 16))) if sel and args.precision == "fp32"
+                        else None),
             "kernel": "k_slab (persistent on-chip PGA phase, fused gather + step)", "selector": sel,
             "launch_us": t * 1e6, "steps_per_launch": ROOF_STEPS, "us_per_step": t * 1e6 / ROOF_STEPS,
             "algorithmic_bytes_per_launch": gathered, "compulsory_dram_bytes_per_launch": compulsory,
@@ -305,88 +317,160 @@ def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle (FP64, one thread) on a bounded sample of the workload:
-    per step, the first phase's momentum PGA for 64 of the 1024 starting
-    points and 100 of the 2000 steps, on both graphs.  Warm-up steps run the
-    same sample untimed."""
-    from oracle import deco_oracle as O
-    gs = graphs()
-    cols = 64
-    steps = 100
-
-    def sample(k):
-        units = 0
-        for g in gs:
-            Y = O.initial_block(g, cols, 1, O.Params(init="idi_half_uniform"), k)
-            O.run_phase(g, Y, O.Phase(1, steps, 0.01, 0.9), O.OBJ_MULTILINEAR01)
-            units += g.nnz * cols * steps
-        return units
-
-    for w in range(args.warmup):
-        sample(1000 + w)
-    sample_units = 0
-    t_total = 0.0
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        sample_units += sample(k)
-        t_total += time.perf_counter() - t0
-    value = sample_units / t_total
-    return {"value": value, "ms": t_total * 1e3 / max(args.steps, 1),
-            "sample": f"per step: first phase only, {cols} of {B} starting points, {steps} of 2000 steps, both graphs"}
+    """The CPU oracle (FP64, one thread) on a bounded sample of the headline
+    workload: per bench step, one of the 1000 FP64 PGA steps of the whole
+    10^6 x 128 block; warm-up steps run the same step untimed."""
+    rate, s_per, sample = oracle_er1m_sample(args.steps, args.warmup)
+    return {"value": rate, "ms": s_per * 1e3, "sample": "per bench step: " + sample}
 
 
-def run_er1m():
-    """Large sparse workload: ER(n = 10^6, average degree 10), B = 128 starts
-    with BF16 iterates, one unlifted phase of T = 1000 steps (alpha = 0.01,
-    plain PGA), IDI-centred starts; rounding, cuts and argmax included.
-
-    Roofline of its dominant kernel (the per-step kernel in the tuned shape),
-    HBM-bound: algorithmic bytes per step = CSR (4 nnz + 4 (n+1)) + read and
-    write of the BF16 block (2 n C 2 B)."""
-    import torch
-    import paper_2509_18612_gb300 as deco
-    from paper_2509_18612_gb300.tuning import TuningTable
-    g = er1m_graph()
+def _er1m_handles(deco, g):
+    """Device graph of the 10^6-node workload and its tuned launch shape for
+    128 BF16 columns (the autotuner times every feasible shape; untimed)."""
     G = deco.graph_from(g)
+    sel, us_probe = deco.deco_autotune(G, ER1M_B, deco.DECO_PREC_BF16, deco.DECO_OBJ_MULTILINEAR01, 0.0, 20)
+    return G, sel, us_probe
+
+
+def step_kernel_roofline(deco, torch, G, g, sel, stream, steps=100):
+    """Roofline of the per-step kernel of the headline workload in its tuned
+    launch shape, timed live: CUDA events on the launching stream around a
+    `steps`-step phase of the 128-column BF16 block (after a short warm-up).
+
+    Algorithmic bytes per step (all C columns): the CSR once (4 nnz + 4 (n+1))
+    plus one read and one write of the BF16 block (2 n C 2 B).  A step of a
+    column-slab shape is S launches, each over an n x w slab (w = C / S); the
+    CSR is then read S times per step, which the algorithmic figure does not
+    count.  Peak: the measured HBM copy bandwidth."""
     C = ER1M_B
-    sel, us_probe = deco.deco_autotune(G, C, deco.DECO_PREC_BF16, deco.DECO_OBJ_MULTILINEAR01, 0.0, 20)
-    p = deco.params(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16)
-    sched = [(1, ER1M_STEPS, 0.01, 0.0)]
-    deco.deco_solve(G, C, [(1, 20, 0.01, 0.0)], p, 1, want_assignment=False, want_phase_cuts=False)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    res, z, _ = deco.deco_solve(G, C, sched, p, 2, want_phase_cuts=False)
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
-    # dominant kernel: CUDA events around 50 steps of the tuned launch shape
     y = (torch.rand(g.n, C, device="cuda") * 2e-4 - 1e-4).to(torch.bfloat16)
-    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, deco.DECO_PREC_BF16, 0.01, 0.0)
-    deco.deco_run_phase(G, C, C, y, None, 4, a, sel)
+    a = deco.step_args(deco.DECO_OBJ_MULTILINEAR01, deco.DECO_PREC_BF16, ER1M_ALPHA, 0.0)
+    deco.deco_run_phase(G, C, C, y, None, 6, a, sel, None, stream)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0.record()
-    deco.deco_run_phase(G, C, C, y, None, 50, a, sel)
-    k1.record()
+    k0.record(stream)
+    deco.deco_run_phase(G, C, C, y, None, steps, a, sel, None, stream)
+    k1.record(stream)
     torch.cuda.synchronize()
-    t_step = k0.elapsed_time(k1) / 1e3 / 50
-    # the same solve with FP32 iterates (cut gap of the precisions)
-    r32, _, _ = deco.deco_solve(G, C, sched, deco.params(init=deco.DECO_INIT_IDI), 2, want_assignment=False,
-                                want_phase_cuts=False)
+    t_step = k0.elapsed_time(k1) / 1e3 / steps
+    slabs = 1 << ((sel >> 16) & 0xF) if (sel & 0xFF) == deco.DECO_KERNEL_GLOBAL and (sel >> 16) & 0xF else 1
     alg = 4 * g.nnz + 4 * (g.n + 1) + 2 * g.n * C * 2
     peaks, kind = measured_peaks()
     ach = alg / t_step / 1e9
-    return {"workload": "ER(n=1e6, avg deg 10); B=128 bf16 starts (IDI); pQUCO T=1000, alpha=0.01",
-            "value": res.edge_updates / t, "unit": "edge-updates/s", "solve_s": t, "best_cut": res.best_cut,
-            "fp32_best_cut": r32.best_cut,
-            "m": g.m, "tuned_kernel": hex(sel), "gpu_launches": res.kernel_launches,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"],
-                         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this
-                         # kernel in this shape (profiles/k_step_global_er1m_bf16.md)
-                         "traffic": K_STEP_ER1M_TRAFFIC if sel == 0x1 else None, "peak_kind": kind,
-                         "kernel": "k_step_global (one step)", "us_per_launch": t_step * 1e6,
-                         "algorithmic_bytes_per_launch": alg}}
+    traffic = DRAM_TRAFFIC.get(("k_step_global", int(sel)))
+    return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_per": "launch" if traffic is not None else None,
+            "peak_kind": kind + " (HBM copy)",
+            "kernel": "k_step_global (fused CSR gather + PGA step, one launch per step and column slab)",
+            "selector": hex(sel), "launches_per_step": slabs, "us_per_step": t_step * 1e6,
+            "us_per_launch": t_step * 1e6 / slabs, "algorithmic_bytes_per_step": alg,
+            "algorithmic_bytes_per_launch": alg if slabs == 1 else
+            4 * g.nnz + 4 * (g.n + 1) + 2 * g.n * (C // slabs) * 2}
+
+
+def run_headline(args, rank, world):
+    """The headline workload, timed: W untimed warm-up solves, then K solves,
+    each bracketed by CUDA events on the solve's stream, with a 256 MB write
+    between them (L2 flush; the 256 MB BF16 block itself is larger than L2)."""
+    import torch
+    import paper_2509_18612_gb300 as deco
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    g = er1m_graph()
+    G, sel, us_probe = _er1m_handles(deco, g)
+    p = deco.params(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16)
+    sched = [(1, ER1M_STEPS, ER1M_ALPHA, 0.0)]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    launches = [0]
+    cuts = []
+
+    def one_step(seed):
+        res, _, _ = deco.deco_solve(G, ER1M_B, sched, p, seed, want_assignment=False, want_phase_cuts=False,
+                                    stream=stream)
+        launches[0] += res.kernel_launches
+        return res
+
+    for w in range(args.warmup):
+        one_step(1000 + w + 7919 * rank)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches[0] = 0
+    units = 0
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            res = one_step(k + 7919 * rank)
+            ev[k][1].record(stream)
+            units += res.edge_updates
+            cuts.append(int(res.best_cut))
+        torch.cuda.synchronize()
+    timed_launches = launches[0]
+    ms, value = whole_job(sum(a.elapsed_time(b) for a, b in ev), units, world, dev)
+
+    # ---- end to end through the public API: CSR from pinned host memory in,
+    # best cut and assignment out, every step
+    e2e = None
+    if rank == 0:
+        rp = torch.from_numpy(g.row_ptr).pin_memory()
+        ci = torch.from_numpy(g.col_idx).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_units = 0
+        for k in range(e2e_steps):
+            Gh = deco.deco_create_graph(g.n, rp.numpy(), ci.numpy(), None, 0)
+            deco.deco_set_tuning(Gh, ER1M_B, deco.DECO_PREC_BF16, sel)   # the recorded shape (no timing)
+            res, z, _ = deco.deco_solve(Gh, ER1M_B, sched, p, 4242 + k, want_phase_cuts=False, stream=stream)
+            Gh.close()
+            e_units += res.edge_updates
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e = {"value": e_units / (t1 - t0), "unit": "edge-updates/s",
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes),
+               "d2h_bytes_per_step": int(g.n + 32), "steps": e2e_steps,
+               "includes": "deco_create_graph from pinned host CSR (validation + upload), deco_solve, "
+                           "assignment download"}
+    roof = step_kernel_roofline(deco, torch, G, g, sel, stream) if rank == 0 else None
+    # the same solve with FP32 iterates: the cut gap of the two precisions at seed 2
+    gap = None
+    if rank == 0:
+        r16, _, _ = deco.deco_solve(G, ER1M_B, sched, p, 2, want_assignment=False, want_phase_cuts=False)
+        r32, _, _ = deco.deco_solve(G, ER1M_B, sched, deco.params(init=deco.DECO_INIT_IDI), 2,
+                                    want_assignment=False, want_phase_cuts=False)
+        gap = {"seed": 2, "bf16_best_cut": int(r16.best_cut), "fp32_best_cut": int(r32.best_cut)}
+    return {"value": value, "ms": ms, "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+            "best_cuts": cuts, "gpu_launches": timed_launches, "tuned_kernel": hex(sel),
+            "autotune_us_per_step": us_probe, "m": g.m, "nnz": g.nnz, "cut_gap_seed2": gap}
+
+
+def oracle_er1m_sample(steps: int, warmup: int = 0):
+    """The CPU oracle (FP64, one thread) on a bounded sample of the headline
+    workload: `steps` PGA steps of the whole 10^6 x 128 block (of the 1000 of
+    a solve), from a seeded explicit start (the oracle's own IDI start draws
+    1.3e8 Gaussians, which alone takes longer than the sample).  Returns
+    (edge-updates per second, seconds per step, sample description)."""
+    from oracle import deco_oracle as O
+    g = er1m_graph()
+    A, d = O.adjacency(g), O.net_degree(g)
+    x0 = gg.uniform_x0(g.n, ER1M_B, 5)
+    Y = O.initial_block(g, ER1M_B, 1, O.Params(init="explicit"), 0, x0=x0)
+    V = np.zeros_like(Y)
+    for _ in range(warmup):
+        Y, V = O.pga_step(g, Y, ER1M_ALPHA, O.OBJ_MULTILINEAR01, V, 0.0, A=A, d=d)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Y, V = O.pga_step(g, Y, ER1M_ALPHA, O.OBJ_MULTILINEAR01, V, 0.0, A=A, d=d)
+    t = time.perf_counter() - t0
+    return (g.nnz * ER1M_B * steps / t, t / max(steps, 1),
+            f"{steps} of the 1000 FP64 PGA steps of the whole n = 10^6 x B = 128 block "
+            f"(scipy CSR x dense, one thread), from a seeded explicit start")
 
 
 def run_er4096_dense():
@@ -748,11 +832,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="deco", choices=["deco", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="iterate precision of the ER(800) + torus workload")
     ap.add_argument("--polish", type=int, default=50)
     ap.add_argument("--no-other", action="store_true", help="skip the other-precision measurement")
     ap.add_argument("--main-only", action="store_true",
-                    help="measure only the main workload (skip the 1M-node and 256-graph workloads)")
+                    help="measure only the headline workload (skip every other workload)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -763,13 +848,12 @@ def main():
         if rank != 0:
             return
         r = run_reference(args, rank, world)
-        cores = 1
         line = {"metric": METRIC, "value": r["value"], "unit": "edge-updates/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-                "cpu_baseline": {"value": r["value"], "unit": "edge-updates/s", "cores": cores,
+                "config": {"workload": HEAD_WORKLOAD, "l2": "n/a (CPU)"},
+                "cpu_baseline": {"value": r["value"], "unit": "edge-updates/s", "cores": 1,
                                  "kind": "oracle", "sample": r["sample"]},
                 "e2e": {"value": r["value"], "unit": "edge-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -780,10 +864,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    r = run_deco(args, rank, world)
+    r = run_headline(args, rank, world)
     extra = {}
     if rank == 0 and not args.main_only:
-        extra["er1m_sparse"] = run_er1m()
+        sub = argparse.Namespace(steps=3, warmup=2, precision=args.precision, polish=args.polish,
+                                 no_other=args.no_other)
+        extra["er800_torus_b1024"] = dict(run_deco(sub, 0, 1), workload=WORKLOAD,
+                                          dtype="bf16" if args.precision == "bf16" else "f32",
+                                          unit="edge-updates/s", steps=sub.steps, warmup=sub.warmup)
         extra["er4096_dense"] = run_er4096_dense()
         extra["greedy_comparison"] = run_greedy_comparison()
         extra["lifting_sweep"] = run_lifting_sweep()
@@ -793,19 +881,19 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1:
-            rr = run_reference(argparse.Namespace(steps=40, warmup=1), 0, 1)   # ~10 s of CPU work
-            cpu = {"value": rr["value"], "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
-                   "sample": rr["sample"]}
+            rate, _, sample = oracle_er1m_sample(3)   # ~20 s of CPU work
+            cpu = {"value": rate, "unit": "edge-updates/s", "cores": 1, "kind": "oracle", "sample": sample}
         line = {"metric": METRIC, "value": r["value"], "unit": "edge-updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MB write)",
+                "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": HEAD_WORKLOAD,
+                           "l2": "flushed between timed steps (256 MB write); the 256 MB block exceeds L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "clocks": r["clocks"], "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
-                "gpu_launches": r["gpu_launches"], "other_precision": r["other_precision"],
-                "tuned_kernels": r["tuned"],
-                "best_cuts": r["best_cuts"], "workloads": extra}
+                "gpu_launches": r["gpu_launches"], "tuned_kernel": r["tuned_kernel"],
+                "autotune_us_per_step": r["autotune_us_per_step"], "best_cuts": r["best_cuts"],
+                "cut_gap_seed2": r["cut_gap_seed2"], "workloads": extra}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
