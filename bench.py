@@ -480,10 +480,12 @@ def run_er4096_dense():
     (the autotuner's dense shape), with the sparse per-step kernel on the same
     graph for comparison, and once in FP32 (sparse) for the precision's cut gap.
 
-    Roofline of its dominant kernel (k_dense_step), tensor-bound: algorithmic
-    FLOPs per step = 2 n^2 B (the dense product A Y, padding not counted),
-    timed as the difference of 250- and 50-step phases (CUDA events on the
-    launching stream), so the transposed copies in and out are excluded."""
+    Roofline of its dominant kernel (the persistent dense phase kernel),
+    tensor-bound: algorithmic FLOPs per step = 2 nnz B, the method's own work
+    (every stored entry of A times every column; the tensor cores also
+    multiply the zeros of A, 2 n^2 B in all, reported beside it), timed as the
+    difference of 250- and 50-step phases (CUDA events on the launching
+    stream), so the transposed copies in and out are excluded."""
     import torch
     import paper_2509_18612_gb300 as deco
     g = gg.er_graph(DENSE_N, DENSE_P, DENSE_N)
@@ -521,7 +523,8 @@ def run_er4096_dense():
         torch.cuda.synchronize()
         times[steps] = k0.elapsed_time(k1) / 1e3
     t_step = (times[250] - times[50]) / 200
-    flops = 2.0 * g.n * g.n * C
+    flops = 2.0 * g.nnz * C
+    dense_flops = 2.0 * g.n * g.n * C
     peaks, kind = measured_peaks()
     ach = flops / t_step / 1e12
     # tensor-core ceiling of the contraction's instruction shape (M = 128,
@@ -540,7 +543,8 @@ def run_er4096_dense():
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_kind": kind + " (burst)",
                          "kernel": "k_dense_phase (per step of a phase launch)", "us_per_step": t_step * 1e6,
-                         "algorithmic_flops_per_launch": flops,
+                         "algorithmic_flops_per_step": flops, "dense_equivalent_flops_per_step": dense_flops,
+                         "dense_equivalent_tflops": dense_flops / t_step / 1e12,
                          "tensor_ns_per_instruction": issue,
                          "tensor_ceiling_tflops_n128": ceiling,
                          "frac_of_ceiling_n128": ach / ceiling}}
@@ -678,8 +682,41 @@ def run_ba256():
             "round_best_score": [int(s.max()) for s in ex["round_scores"]]}
 
 
+def run_ba16_cut_gap():
+    """Cut gap of the batched population search against the FP64 oracle: the
+    first 16 graphs of the 256-graph family (the oracle's batched search over
+    all 256 would take hours on one core; its evolution ranks candidates by
+    cuts summed over the batch, so the subset runs as a batch of its own on
+    both sides), B = 256, 32 candidates x 8 starts, 5 rounds, lift 1 / 2,
+    T ~ U{500..2000}, e ~ U[-4, -1], momentum 0.9, IDI + uniform starts,
+    seed 2, with FP32 and with BF16 iterates.  The oracle's run is
+    oracle/reference_cuts.py batch16."""
+    import paper_2509_18612_gb300 as deco
+    rng = np.random.default_rng(3000)
+    sizes = rng.integers(200, 1201, 256)[:16]
+    graphs_ = [gg.ba_graph(int(n), 4, 3000 + i) for i, n in enumerate(sizes)]
+    batch = deco.deco_create_batch([deco.graph_from(g) for g in graphs_])
+    pop = deco.population(candidates=32, rounds=5, t_lo=500, t_hi=2000, e_lo=-4.0, e_hi=-1.0, momentum=0.9,
+                          lifts=(1, 2))
+    out = {"graphs": 16, "seed": 2}
+    for label, prec in (("fp32", deco.DECO_PREC_FP32), ("bf16", deco.DECO_PREC_BF16)):
+        p = deco.params(init=deco.DECO_INIT_IDI_HALF_UNIFORM, precision=prec)
+        res, best, ex = deco.deco_solve_batch(batch, 256, p, pop, 2)
+        out[label] = {"best_cuts": [int(x) for x in best], "sum_best_cuts": int(best.sum()),
+                      "final_T": [int(x) for x in ex["final_T"]], "device_s": res.device_ms / 1e3}
+    return out
+
+
 LEARNED_BUDGETS = [int(round(25 * 2 ** (k / 2))) for k in range(17)]   # 25, 35, 50, ..., 6400
-LEARNED_SEEDS = (11, 12, 13)
+LEARNED_SEEDS = tuple(range(11, 27))   # 16 solver seeds
+
+
+def _quantiles(xs):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    q = lambda f: float(np.quantile(np.asarray(xs), f))  # noqa: E731
+    return {"min": xs[0], "q25": q(0.25), "median": q(0.5), "q75": q(0.75), "max": xs[-1]}
 
 
 def run_learned():
@@ -693,11 +730,15 @@ def run_learned():
     (IDI starts, 4 x (1000 unlifted + 250 lifted) steps); each start method
     runs the same pDECO structure, 2 x (T unlifted + T/4 lifted), momentum
     0.9, with budgets T = 25 * 2^(k/2) (25, 35, 50, ..., 6400) and reports,
-    for each of three solver seeds, the first budget whose best cut is within
+    for each of 16 solver seeds, the first budget whose best cut is within
     0.1 % of the target, with its device time (the learned proposal's
-    inference time included).  A seed that never reaches the target counts
-    as infinitely slow; the speed-up is the ratio of the median times over
-    the seeds (defined when at least two of the three reach the target)."""
+    inference time included).  Methods: the learned mean with BF16 iterates,
+    IDI with BF16 iterates (the same per-step cost: the fair comparison of the
+    starts), IDI with FP32 iterates (the plain solver) and uniform FP32
+    starts.  Reported per method: the fraction of seeds that reach the target
+    and the quartiles of their device times; the speed-ups are ratios of the
+    medians over the seeds that reached the target.  Also the rounded mean
+    itself: the cut of z = 1{h > 0} for the learned h and for IDI's h."""
     import torch
     import paper_2509_18612_gb300 as deco
     rng = np.random.default_rng(5000)
@@ -729,7 +770,8 @@ def run_learned():
     train_s = a.elapsed_time(b) / 1e3
 
     out = {"train_graphs": len(train), "label_s": label_s, "train_s": train_s, "train_steps": 400,
-           "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "eval": {}}
+           "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "seeds": len(LEARNED_SEEDS),
+           "eval": {}}
     Bv = 256
     for name, g in (("ba2000_m4", gg.ba_graph(2000, 4, 9001)), ("er5000_p0.002", gg.er_graph(5000, 0.002, 9002))):
         G = deco.graph_from(g)
@@ -738,8 +780,16 @@ def run_learned():
         target = tres.best_cut
         h = torch.zeros(g.n, device="cuda")
         model.infer(G, h, feat_seed=7, precision=deco.DECO_PREC_BF16)   # warm-up
+        hi = torch.zeros(g.n, device="cuda")
+        rounded = {"learned": deco.deco_eval_cut(G, (h > 0).to(torch.uint8).cpu().numpy()), "idi": []}
+        for seed in LEARNED_SEEDS[:8]:
+            deco.deco_idi_mean(G, 0.2, seed, 0, hi)
+            torch.cuda.synchronize()
+            rounded["idi"].append(deco.deco_eval_cut(G, (hi > 0).to(torch.uint8).cpu().numpy()))
+        rounded["idi_mean_over_8_draws"] = float(np.mean(rounded["idi"]))
         methods = {
             "learned_bf16": deco.params(init=deco.DECO_INIT_MEAN, precision=deco.DECO_PREC_BF16),
+            "idi_bf16": deco.params(init=deco.DECO_INIT_IDI, precision=deco.DECO_PREC_BF16),
             "idi_fp32": deco.params(init=deco.DECO_INIT_IDI),
             "uniform_fp32": deco.params(init=deco.DECO_INIT_UNIFORM, uniform_half_width=1e-4),
         }
@@ -765,14 +815,20 @@ def run_learned():
                         rec["reached"] = True
                         break
                 runs.append(rec)
-            med = statistics.median(x["device_s"] if x["reached"] else float("inf") for x in runs)
-            res_m[mname] = {"reached_seeds": sum(x["reached"] for x in runs), "runs": runs,
-                            "median_device_s": med if med != float("inf") else None}
-        speed = None
-        if res_m["learned_bf16"]["median_device_s"] and res_m["idi_fp32"]["median_device_s"]:
-            speed = res_m["idi_fp32"]["median_device_s"] / res_m["learned_bf16"]["median_device_s"]
-        out["eval"][name] = {"n": g.n, "m": g.m, "target_cut": int(target), "methods": res_m,
-                             "speedup_learned_vs_idi": speed}
+            reached = [x["device_s"] for x in runs if x["reached"]]
+            res_m[mname] = {"reached_fraction": len(reached) / len(runs), "device_s": _quantiles(reached),
+                            "budgets": _quantiles([x["budget"] for x in runs if x["reached"]]),
+                            "runs": [[x["seed"], x["reached"], x["budget"], round(x["device_s"], 6), x["best_cut"]]
+                                     for x in runs]}
+
+        def ratio(x, y):
+            qa, qb = res_m[x]["device_s"], res_m[y]["device_s"]
+            return qa["median"] / qb["median"] if qa and qb else None
+        out["eval"][name] = {"n": g.n, "m": g.m, "target_cut": int(target), "rounded_mean_cut": rounded,
+                             "methods": res_m,
+                             "speedup_learned_bf16_vs_idi_bf16": ratio("idi_bf16", "learned_bf16"),
+                             "speedup_learned_bf16_vs_idi_fp32": ratio("idi_fp32", "learned_bf16"),
+                             "speedup_learned_bf16_vs_uniform_fp32": ratio("uniform_fp32", "learned_bf16")}
     return out
 
 
@@ -877,6 +933,7 @@ def main():
         extra["lifting_sweep"] = run_lifting_sweep()
         extra["init_ablation"] = run_init_ablation()
         extra["ba256_population"] = run_ba256()
+        extra["ba16_population_cut_gap"] = run_ba16_cut_gap()
         extra["learned_proposal"] = run_learned()
     if rank == 0:
         cpu = None

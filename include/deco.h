@@ -140,6 +140,27 @@ typedef enum deco_status {
  * Same iterates as the other forms.  DECO_KERNEL_AUTO without a recorded
  * tuning, and the batched on-chip launch of deco_solve_batch, use this form. */
 #define DECO_KERNEL_ROW_PAIRS (1 << 21)
+/* With DECO_KERNEL_GLOBAL (optionally with column slabs), the pipelined form
+ * of the per-step kernel: rows sorted by degree in slices of 32 / G rows (G
+ * lanes per row, 16 bytes of the row per lane), every neighbour row copied
+ * into shared memory (cp.async) several slices ahead of its use, so each warp
+ * keeps a few slices of gathers in flight.  The sliced copy of the CSR is
+ * built on first use and kept with the graph.  Same iterates as the other
+ * forms (every row summed in the same order).  Its shape:
+ *   DECO_KERNEL_PIPE_ENTRIES(e)  entries of a row per stage: e = 0: 16,
+ *                                1: 8, 2: 24, 3: 32 (longer rows go in parts)
+ *   DECO_KERNEL_PIPE_STAGES(s)   shared-memory stages per warp: s = 0: 3,
+ *                                1: 2, 2: 4
+ *   DECO_KERNEL_PIPE_WARPS(w)    warps per block: w = 0: as many as fit
+ *                                (at most 8), 1..7: w */
+#define DECO_KERNEL_PIPELINED (1 << 22)
+#define DECO_KERNEL_PIPE_ENTRIES(e) ((e) << 23)
+#define DECO_KERNEL_PIPE_STAGES(s) ((s) << 25)
+#define DECO_KERNEL_PIPE_WARPS(w) ((w) << 27)
+/* With DECO_KERNEL_PIPELINED and BF16 blocks of unit-weight graphs: the sums
+ * use Blackwell's mixed-precision add (BF16 operand widened exactly, one FP32
+ * rounding), the same operation as widening first and adding. */
+#define DECO_KERNEL_PIPE_MIXED_ADD (1 << 30)
 
 /* deco_create_graph flags */
 #define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */

@@ -49,6 +49,28 @@ DECO_KERNEL_DENSE = 3
 DECO_KERNEL_DENSE_PER_STEP = 1 << 12
 DECO_KERNEL_LEAN = 1 << 20
 DECO_KERNEL_ROW_PAIRS = 1 << 21
+DECO_KERNEL_PIPELINED = 1 << 22
+DECO_KERNEL_PIPE_MIXED_ADD = 1 << 30
+
+
+def DECO_KERNEL_PIPE_ENTRIES(e: int) -> int:
+    """Entries of a row per stage of the pipelined form: e = 0: 16, 1: 8, 2: 24, 3: 32."""
+    return e << 23
+
+
+def DECO_KERNEL_PIPE_STAGES(s: int) -> int:
+    """Shared-memory stages per warp of the pipelined form: s = 0: 3, 1: 2, 2: 4."""
+    return s << 25
+
+
+def DECO_KERNEL_PIPE_WARPS(w: int) -> int:
+    """Warps per block of the pipelined form: 0 = as many as fit (at most 8), 1..7."""
+    return w << 27
+
+
+def DECO_KERNEL_COLUMN_SLABS(s: int) -> int:
+    """2^s column slabs run one after another (with DECO_KERNEL_GLOBAL)."""
+    return s << 16
 
 # every function include/deco.h declares (checked by the CPU test-suite)
 EXPORTED = [

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,23 @@ struct SlabImage {
   int32_t max_words = 0;             // largest part in 32-bit words
 };
 
+// Sliced copy of the CSR for the pipelined per-step kernel (step_sell.cu),
+// built once per slice height and kept with the graph: rows sorted by degree
+// (largest first, ties by index) in slices of ng rows; slice s holds
+// width[s] entries per row, entry k of its row i at off[s] + k * ng + i
+// (column index, with the sign of a +-1 weight in bit 31; 0xFFFFFFFF past the
+// row's degree).
+struct SellImage {
+  int ng = 0;
+  int32_t nslices = 0;
+  std::vector<int32_t> width;   // host copy of the widths
+  int64_t* off = nullptr;       // device, nslices + 1
+  int2* rows = nullptr;         // device, nslices * ng: (row, degree); (-1, 0) past the last row
+  int32_t* width_d = nullptr;   // device, nslices
+  uint32_t* idx = nullptr;      // device entries
+  float* w = nullptr;           // device weights in the same layout (general weights only)
+};
+
 // The opaque handle of the ABI.
 struct deco_graph {
   int32_t n = 0;
@@ -73,6 +91,8 @@ struct deco_graph {
   std::vector<int32_t> h_col;       // host copy of the device edge order
   std::vector<float> h_w;           // host copy of the device-order weights (or empty)
   std::vector<SlabImage> images;    // on-chip CSR images, one per cluster size used
+  std::deque<SellImage> sells;      // sliced CSR copies of the pipelined step kernel, one per slice height
+                                    // (a deque: phase plans keep pointers to them while others are added)
   __nv_bfloat16* dense = nullptr;   // dense BF16 copy of A for the tensor-core kernel (built on first use)
   int32_t dense_ld = 0;             // its row stride, round_up(n, 128)
   struct Tuning {
@@ -151,6 +171,16 @@ struct StepLaunch {
   int32_t* flag;
 };
 int launch_step_global(const StepLaunch& s, cudaStream_t st);
+// The pipelined form of the same step (bit-identical iterates): `im` from
+// sell_image(g, 32 / sell_group_lanes(C, precision)); maxe entries per part,
+// `stages` shared-memory stages, wpb warps per block; mixed_add: BF16 sums
+// of unit-weight rows with the mixed-precision add instruction (same result).
+int launch_step_sell(const StepLaunch& s, const SellImage& im, int maxe, int stages, int wpb, bool mixed_add,
+                     cudaStream_t st);
+int sell_group_lanes(int32_t C, int prec);
+int sell_image(deco_graph* g, int ng, const SellImage** out);
+void free_sell_image(SellImage& im);
+size_t sell_smem_bytes(int32_t C, int prec, int maxe, int stages, int wpb, bool mom, bool weighted);
 // row-major n x ld (columns < C)  <->  S dense slabs of n x w (column c in slab c / w)
 int launch_slab_layout(int32_t n, int32_t ld, int32_t C, int32_t w, int32_t S, size_t esz, const void* src,
                        void* dst, bool to_slabs, cudaStream_t st);

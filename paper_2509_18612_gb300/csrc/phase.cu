@@ -66,7 +66,14 @@ bool valid_selector(int kernel) {
   const int s = (kernel >> 16) & 0xF;
   const int lean = (kernel >> 20) & 1;
   const int pairs = (kernel >> 21) & 1;
-  if (kernel & ~0x3FFFFF) return false;
+  const int pipe = (kernel >> 22) & 1;
+  const int pipe_shape = (kernel >> 23) & 0x7F;   // entries, stages, warps
+  const int mixed = (kernel >> 30) & 1;
+  if (kernel & ~0x7FFFFFFF) return false;
+  if (mixed && !pipe) return false;
+  if (pipe && kind != DECO_KERNEL_GLOBAL) return false;
+  if (!pipe && pipe_shape) return false;
+  if (pipe && ((pipe_shape >> 2) & 3) == 3) return false;   // stage code 3 is not defined
   if (lean && kind != DECO_KERNEL_ONCHIP) return false;
   if (pairs && kind != DECO_KERNEL_ONCHIP) return false;
   if (lean && x == 1) return false;   // the lean form exchanges through L2
@@ -157,6 +164,9 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_x = (force >> 14) & 0x3;
   const int want_s = (force >> 16) & 0xF;
   const bool want_lean = ((force >> 20) & 1) != 0;
+  const bool want_pipe = ((force >> 22) & 1) != 0;
+  const int pipe_e = (force >> 23) & 3, pipe_s = (force >> 25) & 3, pipe_w = (force >> 27) & 7;
+  const bool pipe_mix = ((force >> 30) & 1) != 0;
   // the row-pair form is also the cost model's choice (measured faster on
   // every on-chip shape of the benchmark); the autotuner times both forms
   const bool want_pairs = ((force >> 21) & 1) != 0 || (force & 0xFF) == DECO_KERNEL_AUTO;
@@ -171,6 +181,15 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   plan->lean = want_lean;
   plan->pairs = want_pairs;
   if (force == DECO_KERNEL_GLOBAL) {
+    if (want_pipe) {
+      static const int entries[4] = {16, 8, 24, 32};
+      static const int stages[3] = {3, 2, 4};
+      plan->pipe = true;
+      plan->pipe_maxe = entries[pipe_e];
+      plan->pipe_stages = stages[pipe_s];
+      plan->pipe_wpb = pipe_w;
+      plan->pipe_mixed = pipe_mix;
+    }
     if (want_s) {
       // column slabs of width w, run one after another in a slab-major copy
       const int S = 1 << want_s;
@@ -181,6 +200,24 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
       }
       plan->col_slabs = S;
       plan->slab_w = w;
+    }
+    if (plan->pipe) {
+      // warps per block: as many as the shared memory holds (at most 8), or the given count
+      const int cols = plan->col_slabs > 1 ? plan->slab_w : C;
+      const int max_smem = slab_max_smem();
+      int wpb = plan->pipe_wpb;
+      if (!wpb) {
+        wpb = 8;
+        while (wpb > 1 && sell_smem_bytes(cols, prec, plan->pipe_maxe, plan->pipe_stages, wpb, true, true) >
+                              (size_t)max_smem)
+          --wpb;
+      }
+      if (sell_smem_bytes(cols, prec, plan->pipe_maxe, plan->pipe_stages, wpb, true, true) > (size_t)max_smem) {
+        set_error("the pipelined step kernel does not fit %d warps of %d entries x %d stages", wpb,
+                  plan->pipe_maxe, plan->pipe_stages);
+        return DECO_ERR_UNSUPPORTED;
+      }
+      plan->pipe_wpb = wpb;
     }
     return DECO_OK;
   }
@@ -259,6 +296,12 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
         return cuda_fail(e, "cudaMallocAsync(grid barrier)");
     }
     return dense_make_maps(g->dense, plan.kpad, yt, plan.cpad, plan.dpersist ? plan.dphase.w : 0, maps);
+  }
+  if (plan.kernel == KERNEL_GLOBAL && plan.pipe) {
+    std::lock_guard<std::mutex> lock(g_image_mutex);
+    // the sliced copy lives with the graph, like the on-chip CSR images
+    const int cols = plan.col_slabs > 1 ? plan.slab_w : C;
+    return sell_image(const_cast<deco_graph*>(g), 32 / sell_group_lanes(cols, prec), &plan.sell);
   }
   if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
   {
@@ -373,6 +416,12 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     if (kernels) *kernels += (done ? 1 : steps) + 2 + (momv ? 1 + (store_v ? 1 : 0) : 0);
     return DECO_OK;
   }
+  // one step: the pipelined form where planned, else the lane-group form
+  auto step_launch = [&](const StepLaunch& s, cudaStream_t stream) -> int {
+    if (plan.pipe)
+      return launch_step_sell(s, *plan.sell, plan.pipe_maxe, plan.pipe_stages, plan.pipe_wpb, plan.pipe_mixed, stream);
+    return launch_step_global(s, stream);
+  };
   StepLaunch sl{};
   sl.n = g->n; sl.C = C; sl.ld = ld;
   sl.precision = prec; sl.objective = objective; sl.wmode = g->wmode;
@@ -420,7 +469,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
         sl.yin = blk[c];
         sl.yout = blk[c ^ 1];
         sl.t = t;
-        if ((rc = launch_step_global(sl, st))) return rc;
+        if ((rc = step_launch(sl, st))) return rc;
         c ^= 1;
       }
     }
@@ -434,7 +483,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
     sl.yin = y[cur];
     sl.yout = y[cur ^ 1];
     sl.t = t;
-    int rc = launch_step_global(sl, st);
+    int rc = step_launch(sl, st);
     if (rc) return rc;
     cur ^= 1;
   }

@@ -11,8 +11,12 @@ can compute one by one:
     64 sampled columns of four graphs; >= 99 % identical;
   * the large sparse workload (ER, n = 10^6, average degree 10, B = 128, BF16): the IDI
     mean bit-exact in full; one step from a dyadic block (every partial sum
-    exact in FP32) on 1024 sampled rows within one bf16 rounding; rounding and
-    cuts of that block bit-exact in full;
+    exact in FP32), in the tuned launch shape, against the oracle's step on
+    16 sampled columns (every row, the columns are independent) within one
+    bf16 rounding; one FP32 step from a general block likewise within
+    1e-5 max(1, |y|); rounding and cuts of that block bit-exact in full; ten
+    steps of the pipelined form bit-identical to the lane-group form, in BF16
+    and FP32, with and without column slabs;
   * the learned proposal's evaluation graphs (BA(2000, 4), ER(5000, 0.002)): the network's proposal within
     1e-5 of the oracle's at every node.
 """
@@ -115,20 +119,54 @@ def test_er1m_sparse_step_and_cuts(er1m):
     ref_cuts = np.concatenate([O.cut_values(g, Zd[:, c:c + 16]) for c in range(0, C, 16)])
     np.testing.assert_array_equal(cuts.cpu().numpy(), ref_cuts)
     assert int(best.item()) == O.best_of(ref_cuts)
-    # one step in the tuned shape, 1024 sampled rows against the definition
+    # one step in the tuned shape; the oracle's step (FP64) on 16 sampled
+    # columns, every row
     a = deco.step_args(MUL, deco.DECO_PREC_BF16, 0.01, 0.0)
     flag = torch.zeros(1, dtype=torch.int32, device=DEV)
     deco.deco_run_phase(G, C, C, y, None, 1, a, sel, flag)
     torch.cuda.synchronize()
     assert int(flag.item()) == 0
-    rows = np.sort(np.random.default_rng(9).choice(g.n, 1024, replace=False))
-    A = O.adjacency(g)
-    X = (1.0 + Yd.astype(np.float64)) / 2.0
-    d = O.net_degree(g)
-    Gr = d[rows, None] - 2.0 * (A[rows] @ X)
-    ref = 2.0 * np.clip(X[rows] + 0.01 * Gr, 0.0, 1.0) - 1.0
-    out = y[torch.from_numpy(rows).to(DEV)].float().cpu().numpy().astype(np.float64)
+    cols = np.sort(np.random.default_rng(9).choice(C, 16, replace=False))
+    A, d = O.adjacency(g), O.net_degree(g)
+    ref, _ = O.pga_step(g, Yd[:, cols].astype(np.float64), 0.01, O.OBJ_MULTILINEAR01, A=A, d=d)
+    out = y[:, torch.from_numpy(cols).to(DEV)].float().cpu().numpy().astype(np.float64)
     assert np.all(np.abs(out - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6)
+
+
+def test_er1m_sparse_fp32_step_matches_oracle(er1m):
+    g, G = er1m
+    C = 128
+    sel, _ = deco.deco_autotune(G, C, deco.DECO_PREC_FP32, MUL, 0.0, 5)
+    rng = np.random.default_rng(10)
+    Y = rng.uniform(-1.0, 1.0, size=(g.n, C)).astype(np.float32)
+    y = torch.from_numpy(Y).to(DEV)
+    a = deco.step_args(MUL, deco.DECO_PREC_FP32, 0.01, 0.0)
+    flag = torch.zeros(1, dtype=torch.int32, device=DEV)
+    deco.deco_run_phase(G, C, C, y, None, 1, a, sel, flag)
+    torch.cuda.synchronize()
+    assert int(flag.item()) == 0
+    cols = np.sort(rng.choice(C, 16, replace=False))
+    ref, _ = O.pga_step(g, Y[:, cols].astype(np.float64), 0.01, O.OBJ_MULTILINEAR01)
+    out = y[:, torch.from_numpy(cols).to(DEV)].cpu().numpy().astype(np.float64)
+    tol = 1e-5 * np.maximum(1.0, np.max(np.abs(ref), axis=0, keepdims=True))
+    assert np.all(np.abs(out - ref) <= tol)
+
+
+@pytest.mark.parametrize("precision", [deco.DECO_PREC_BF16, deco.DECO_PREC_FP32])
+def test_er1m_pipelined_form_bitwise_equals_lane_groups(er1m, precision):
+    g, G = er1m
+    C = 128
+    dt = torch.bfloat16 if precision == deco.DECO_PREC_BF16 else torch.float32
+    y0 = (torch.rand(g.n, C, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3)) * 2 - 1).to(dt)
+    a = deco.step_args(MUL, precision, 0.01, 0.0)
+    pipe = deco.DECO_KERNEL_GLOBAL | deco.DECO_KERNEL_PIPELINED
+    out = []
+    for kern in (deco.DECO_KERNEL_GLOBAL, pipe, pipe | deco.DECO_KERNEL_COLUMN_SLABS(2)):
+        y = y0.clone()
+        deco.deco_run_phase(G, C, C, y, None, 10, a, kern)
+        torch.cuda.synchronize()
+        out.append(y)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("which", ["ba2000", "er5000"])

@@ -117,7 +117,7 @@ def test_training_lowers_the_loss():
     assert losses[-1] < 0.8 * losses[0]
 
 
-def test_trained_proposal_beats_a_random_assignment():
+def test_trained_proposal_against_random_and_idi_starts():
     """What training buys, through the C ABI: the network trained for 100 Adam
     steps on the solver's best assignments of 8 small ER / BA graphs proposes,
     on unseen graphs, a sign pattern h > 0 that cuts well over the m / 2 edges
@@ -151,3 +151,21 @@ def test_trained_proposal_beats_a_random_assignment():
     model.train(batch, zb, steps=100, lr=3e-3, feat_seed=7)
     fr = cut_fractions(model)
     assert fr.min() > 0.56 and fr.mean() > 0.59, fr
+    # Against the method's own start (IDI, Sec. 4.1.2) rounded the same way,
+    # z = 1{h_IDI > 0}, averaged over four IDI draws: IDI's greedy rounding
+    # cuts about 0.59 - 0.64 m on these graphs, and the trained proposal lands
+    # in the same range, not clearly above it -- what the network buys here is
+    # a start as good as IDI's without its greedy pass, not a better one.
+    idi = []
+    for g in held_out:
+        G = deco.graph_from(g)
+        hi = torch.zeros(g.n, device=DEV)
+        vals = []
+        for s in range(4):
+            deco.deco_idi_mean(G, 0.2, 40 + s, 0, hi)
+            torch.cuda.synchronize()
+            vals.append(deco.deco_eval_cut(G, (hi > 0).to(torch.uint8).cpu().numpy()) / g.m)
+        idi.append(np.mean(vals))
+    idi = np.array(idi)
+    assert np.all(idi > 0.56), idi
+    assert fr.mean() > 0.92 * idi.mean(), (fr, idi)

@@ -179,9 +179,11 @@ def test_nonfinite_flag():
 
 # -------------------------------------------------- rounding + cut + argmax
 
-@pytest.mark.parametrize("lift", [1, 2, 3])
+@pytest.mark.parametrize("lift", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
 def test_round_cut_bit_exact(lift, precision):
+    # l = 4 and 8: the lifting sweep's larger lifts (Table 2's ablation), where
+    # the FP32 order of the row sum of Eq. 11 decides near-ties
     g = GRAPHS["signed"]() if lift == 3 else gg.er_graph(800, 0.06, 1)
     rng = np.random.default_rng(lift)
     B = 45
@@ -192,6 +194,17 @@ def test_round_cut_bit_exact(lift, precision):
     if lift == 2:
         pair = rng.random((g.n, B)) < 0.1          # exact cancellations y0 = -y1
         Y[:, 1::2] = np.where(pair, -Y[:, 0::2], Y[:, 1::2])
+    if lift >= 4:
+        # exact cancellations in pairs (sum exactly 0: rounds to 1) and
+        # near-cancellations whose FP32 sum depends on the order
+        pair = rng.random((g.n, B)) < 0.1
+        for i in range(1, lift, 2):
+            Y[:, i::lift] = np.where(pair, -Y[:, i - 1::lift], Y[:, i::lift])
+        near = rng.random((g.n, B)) < 0.05
+        Y[:, 0::lift] = np.where(near, np.float32(1.0), Y[:, 0::lift])
+        Y[:, 1::lift] = np.where(near, np.float32(-1.0), Y[:, 1::lift])
+        Y[:, 2::lift] = np.where(near, np.float32(2.0 ** -30), Y[:, 2::lift])
+        Y[:, 3::lift] = np.where(near, np.float32(-2.0 ** -30), Y[:, 3::lift])
     Yp = np.zeros((g.n, ld), np.float32)
     Yp[:, :C] = Y
     dt = torch.bfloat16 if precision == deco.DECO_PREC_BF16 else torch.float32
@@ -219,6 +232,23 @@ def test_round_cut_bit_exact(lift, precision):
     ref = O.cut_values(g, Z)
     np.testing.assert_array_equal(cuts.cpu().numpy(), ref)
     assert int(best.item()) == O.best_of(ref)
+
+
+@pytest.mark.parametrize("lift", [4, 8])
+def test_lifted_phase_large_lift_matches_oracle(lift):
+    # one pLUCO phase (Alg. 2) with l = 4 / 8 columns per start, momentum,
+    # IDI starts drawn on the device: rounded cuts (Eq. 11) identical on >= 99 %
+    # of the starts and the same best cut as the oracle's
+    g = gg.er_graph(400, 0.05, 12)
+    B = 64
+    sched = [(lift, 150, 0.002, 0.9)]
+    G = deco.graph_from(g)
+    res, z, pc = deco.deco_solve(G, B, sched, deco.params(init=deco.DECO_INIT_IDI), 77)
+    ref = O.solve(g, B, [O.Phase(*sched[0])], O.Params(init="idi"), 77)
+    assert _agreement(pc[0], ref.phase_cuts[0]) >= 0.99
+    assert res.best_cut == O.cut_value(g, z)
+    assert res.best_cut == ref.best_cut
+    assert res.edge_updates == g.nnz * B * lift * 150
 
 
 def test_argmax_ties_lowest_index():
