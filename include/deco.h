@@ -123,7 +123,7 @@ typedef enum deco_status {
  * memory stores, or through L2 (global stores + one bulk copy per CTA). */
 #define DECO_KERNEL_EXCHANGE_DSMEM (1 << 14)
 #define DECO_KERNEL_EXCHANGE_L2 (2 << 14)
-/* With DECO_KERNEL_GLOBAL, runs the block as 2^s column slabs (s = 1..6), one
+/* With DECO_KERNEL_GLOBAL, runs the block as 2^s column slabs (s = 1..6; a 3-bit field), one
  * after another: the block is copied into dense n x w slabs (w = C / 2^s
  * rounded up to 8) and every step of a slab runs before the next slab, so a
  * narrow slab of a graph too large for shared memory stays in L2.  Needs
@@ -142,15 +142,21 @@ typedef enum deco_status {
 #define DECO_KERNEL_ROW_PAIRS (1 << 21)
 /* With DECO_KERNEL_GLOBAL (optionally with column slabs), the pipelined form
  * of the per-step kernel: rows sorted by degree in slices of 32 / G rows (G
- * lanes per row, 16 bytes of the row per lane), every neighbour row copied
- * into shared memory (cp.async) several slices ahead of its use, so each warp
- * keeps a few slices of gathers in flight.  The sliced copy of the CSR is
- * built on first use and kept with the graph.  Same iterates as the other
- * forms (every row summed in the same order).  Its shape:
- *   DECO_KERNEL_PIPE_ENTRIES(e)  entries of a row per stage: e = 0: 16,
+ * lanes per row, 16 bytes of the row per lane); slice s belongs to warp
+ * s mod #warps, whose items (a slice, or a part of `entries` entries of a
+ * slice with longer rows) form one contiguous stream of fixed-size records
+ * (rows, counts, padded column indices), built on first use for the graph and
+ * launch shape and kept with the graph.  A warp copies each record into shared
+ * memory (cp.async) 2S - 1 items ahead and the neighbour rows of each item
+ * S - 1 items ahead, and sums an item's rows in CSR order from shared memory.
+ * Same iterates as the other forms.  Its shape:
+ *   DECO_KERNEL_PIPE_ENTRIES(e)  entries of a row per item: e = 0: 16,
  *                                1: 8, 2: 24, 3: 32 (longer rows go in parts)
  *   DECO_KERNEL_PIPE_STAGES(s)   shared-memory stages per warp: s = 0: 3,
- *                                1: 2, 2: 4
+ *                                1: 2, 2: 4; s = 3: the register form (no
+ *                                gather stages: each lane loads its 16 bytes
+ *                                of the item's rows into registers; 8 or 16
+ *                                entries only), for L2-resident column slabs
  *   DECO_KERNEL_PIPE_WARPS(w)    warps per block: w = 0: as many as fit
  *                                (at most 8), 1..7: w */
 #define DECO_KERNEL_PIPELINED (1 << 22)
@@ -161,6 +167,10 @@ typedef enum deco_status {
  * use Blackwell's mixed-precision add (BF16 operand widened exactly, one FP32
  * rounding), the same operation as widening first and adding. */
 #define DECO_KERNEL_PIPE_MIXED_ADD (1 << 30)
+/* With DECO_KERNEL_PIPELINED: the records and the new rows are read and
+ * written with the L2 evict-first priority, so that L2 keeps the block (or
+ * column slab) being gathered.  Same iterates. */
+#define DECO_KERNEL_PIPE_L2_HINTS (1 << 19)
 
 /* deco_create_graph flags */
 #define DECO_GRAPH_SKIP_SYMMETRY_CHECK 0x1u  /* caller guarantees symmetry */

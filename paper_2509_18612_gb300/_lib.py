@@ -51,6 +51,7 @@ DECO_KERNEL_LEAN = 1 << 20
 DECO_KERNEL_ROW_PAIRS = 1 << 21
 DECO_KERNEL_PIPELINED = 1 << 22
 DECO_KERNEL_PIPE_MIXED_ADD = 1 << 30
+DECO_KERNEL_PIPE_L2_HINTS = 1 << 19
 
 
 def DECO_KERNEL_PIPE_ENTRIES(e: int) -> int:

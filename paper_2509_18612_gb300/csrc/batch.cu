@@ -10,12 +10,12 @@
 // every graph's iterate slab fits in shared memory: one on-chip launch whose
 // items are (graph, 128-byte column slab), each graph's replica on chip;
 // otherwise the per-step kernels over the union).  Rounds
-// alternate the lift as listed (Alg. 3); between rounds the host ranks the
-// candidates (sum over graphs of the candidate's best cut) and replaces the
-// bottom half by perturbed copies of the top half.  From a lift's second
-// round on, the phase and its bookkeeping are replayed from a captured CUDA
-// graph; only the new step sizes / budgets and the starting block are
-// written before each replay.
+// alternate the lift as listed (Alg. 3); after every round a device kernel
+// ranks the candidates (sum over graphs of the candidate's best cut) and
+// replaces the bottom half by perturbed copies of the top half, and the next
+// round's set-up kernel turns the population into the per-column step sizes
+// and budgets.  No round needs the host, so all rounds of a solve are
+// captured in one CUDA graph and launched once.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -156,6 +156,93 @@ __global__ void k_extract_graphs(int32_t n, int32_t W, const uint32_t* zbits, co
   round_best_z[v] = z;
   if (improved[g]) best_z[v] = z;
 }
+
+// ---- the population on the device (Sec. 4.3), so that the rounds of a
+// batched solve run back to back (and are captured in one CUDA graph)
+// without a trip to the host.  Population state: e (FP64 exponents,
+// alpha = 10^e), T (step budgets).
+
+// Round set-up: column c of the block belongs to candidate k = (c / l) / (B / P);
+// its step size (float)10^{e_k} and budget T_k; the round's longest budget;
+// the population the round runs with (kept for the caller).
+__global__ void k_pop_columns(int32_t C, int32_t lift, int32_t per, int32_t P, const double* e, const int32_t* T,
+                              float* alpha_cols, int32_t* steps_cols, int32_t* tmax, double* hist_e,
+                              int32_t* hist_T) {
+  __shared__ int32_t smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  int32_t m = 0;
+  for (int32_t c = threadIdx.x; c < C; c += blockDim.x) {
+    const int32_t k = (c / lift) / per;
+    alpha_cols[c] = (float)pow(10.0, e[k]);
+    steps_cols[c] = T[k];
+    m = max(m, T[k]);
+  }
+  atomicMax(&smax, m);
+  for (int32_t k = threadIdx.x; k < P; k += blockDim.x) {
+    hist_e[k] = e[k];
+    hist_T[k] = T[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *tmax = smax;
+}
+
+// Round close (one block, P <= blockDim.x): the score of candidate k is the
+// sum over graphs of the best cut among its starts; the round's scores (and
+// cuts, if kept) are stored; unless it is the last round, the population
+// evolves: candidates ranked by score (descending, ties keep the lower
+// index), the top half kept, the j-th worst replaced from the j-th best kept
+// with e' = Proj[e_lo, e_hi](e + 0.2 eps), T' = Proj[t_lo, t_hi](floor(T (1 +
+// 0.2 (2 eps' - 1)))), eps ~ N(0,1) by Box-Muller and eps' ~ U(0,1) from
+// Philox counter (j, round, 1, STREAM_EVOLVE).
+__global__ void k_pop_close(int32_t r, int32_t G, int32_t B, int32_t P, const int64_t* cuts, double* e, int32_t* T,
+                            long long* scores_out, int64_t* cuts_out, int32_t evolve, uint32_t k0, uint32_t k1,
+                            double e_lo, double e_hi, int32_t t_lo, int32_t t_hi) {
+  extern __shared__ __align__(8) unsigned char sm_pop[];
+  long long* score = reinterpret_cast<long long*>(sm_pop);
+  double* e0 = reinterpret_cast<double*>(score + P);
+  int32_t* T0 = reinterpret_cast<int32_t*>(e0 + P);
+  int32_t* order = T0 + P;
+  const int32_t per = B / P;
+  for (int32_t k = threadIdx.x; k < P; k += blockDim.x) {
+    long long sc = 0;
+    for (int32_t g = 0; g < G; ++g) {
+      long long m = LLONG_MIN;
+      for (int32_t j = k * per; j < (k + 1) * per; ++j) m = max(m, (long long)cuts[(size_t)g * B + j]);
+      sc += m;
+    }
+    score[k] = sc;
+    scores_out[k] = sc;
+    e0[k] = e[k];
+    T0[k] = T[k];
+  }
+  if (cuts_out)
+    for (int64_t i = threadIdx.x; i < (int64_t)G * B; i += blockDim.x) cuts_out[i] = cuts[i];
+  __syncthreads();
+  if (!evolve) return;
+  for (int32_t k = threadIdx.x; k < P; k += blockDim.x) {
+    int32_t rank = 0;
+    for (int32_t j = 0; j < P; ++j) rank += (score[j] > score[k]) || (score[j] == score[k] && j < k);
+    order[rank] = k;
+  }
+  __syncthreads();
+  const int32_t nkeep = P / 2, nrep = P - nkeep;
+  for (int32_t j = threadIdx.x; j < nrep; j += blockDim.x) {
+    const int32_t victim = order[P - 1 - j];
+    const int32_t src = order[nkeep > 0 ? j % nkeep : 0];
+    const uint4 c = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)r, 1u, STREAM_EVOLVE), k0, k1);
+    const double u1 = (2.0 * (double)(c.x >> 9) + 1.0) * 5.9604644775390625e-8;
+    const double u2 = (2.0 * (double)(c.y >> 9) + 1.0) * 5.9604644775390625e-8;
+    const double u3 = (2.0 * (double)(c.z >> 9) + 1.0) * 5.9604644775390625e-8;
+    const double kPi = 3.141592653589793;
+    const double eps = sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2);
+    e[victim] = fmin(fmax(e0[src] + 0.2 * eps, e_lo), e_hi);
+    const double t = floor((double)T0[src] * (1.0 + 0.2 * (2.0 * u3 - 1.0)));
+    T[victim] = (int32_t)fmin(fmax(t, (double)t_lo), (double)t_hi);
+  }
+}
+
+__global__ void k_fill_round(int32_t r, int32_t* d_round) { *d_round = r; }
 
 __global__ void k_fill_ll(int32_t n, long long v, long long* p) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,9 +566,6 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
       int lift = 0;
       PhaseRunner R;
       BatchSlab S;     // the batched on-chip launch, when every graph fits
-      int uses = 0;
-      int32_t cap_steps = -1;
-      cudaGraphExec_t exec = nullptr;
     };
     std::vector<std::unique_ptr<Lane>> lanes;
     struct Cleanup {
@@ -489,7 +573,6 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
       cudaStream_t st;
       ~Cleanup() {
         for (auto& x : *l) {
-          if (x->exec) cudaGraphExecDestroy(x->exec);
           x->R.release(st);
           cudaStreamSynchronize(st);   // no launch still reads the on-chip parameters
           x->S.release();
@@ -521,54 +604,76 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
     DECO_CUDA_TRY(cudaEventRecord(ev0, st));
 
     const int32_t per = B / P;
-    std::vector<float> h_alpha(Cmax);
-    std::vector<int32_t> h_steps(Cmax);
-    std::vector<int64_t> h_cuts((size_t)G * B);
-    for (int32_t r = 0; r < pop->rounds; ++r) {
-      NvtxRange r_round("deco batch round");
-      const int32_t lift = pop->lifts[r % pop->n_lifts];
-      const int32_t C = B * lift;
-      int32_t tmax = 0;
-      for (int32_t c = 0; c < C; ++c) {
-        const int32_t k = (c / lift) / per;
-        h_alpha[c] = (float)std::pow(10.0, e[k]);
-        h_steps[c] = (int32_t)T[k];
-        tmax = std::max<int32_t>(tmax, (int32_t)T[k]);
-      }
-      DECO_CUDA_TRY(cudaMemcpyAsync(alpha_cols, h_alpha.data(), sizeof(float) * C, cudaMemcpyHostToDevice, st));
-      DECO_CUDA_TRY(cudaMemcpyAsync(steps_cols, h_steps.data(), sizeof(int32_t) * C, cudaMemcpyHostToDevice, st));
-      DECO_CUDA_TRY(cudaMemcpyAsync(d_round, &r, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // population on the device: e, T, the round's longest budget, the
+    // population of every round, the round scores (and cuts, if kept)
+    double *d_e = nullptr, *d_hist_e = nullptr;
+    int32_t *d_T = nullptr, *d_hist_T = nullptr, *d_tmax = nullptr;
+    long long* d_scores = nullptr;
+    int64_t* d_rcuts = nullptr;
+    const int32_t R = pop->rounds;
+    if ((rc = s.alloc(&d_e, sizeof(double) * P)) || (rc = s.alloc(&d_T, sizeof(int32_t) * P)) ||
+        (rc = s.alloc(&d_hist_e, sizeof(double) * (size_t)R * P)) ||
+        (rc = s.alloc(&d_hist_T, sizeof(int32_t) * (size_t)R * P)) || (rc = s.alloc(&d_tmax, sizeof(int32_t) * R)) ||
+        (rc = s.alloc(&d_scores, sizeof(long long) * (size_t)R * P)))
+      return rc;
+    if (round_cuts && (rc = s.alloc(&d_rcuts, sizeof(int64_t) * (size_t)R * G * B))) return rc;
+    {
+      std::vector<int32_t> T32(P);
+      for (int32_t k = 0; k < P; ++k) T32[k] = (int32_t)T[k];
+      DECO_CUDA_TRY(cudaMemcpyAsync(d_e, e.data(), sizeof(double) * P, cudaMemcpyHostToDevice, st));
+      DECO_CUDA_TRY(cudaMemcpyAsync(d_T, T32.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+    }
+    const size_t close_smem = (size_t)P * (sizeof(long long) + sizeof(double) + 2 * sizeof(int32_t));
+    if (P > 1024 || close_smem > 48 * 1024) {
+      set_error("population of %d candidates: at most 1024 in a batched solve", P);
+      return DECO_ERR_UNSUPPORTED;
+    }
 
-      // starting block of this round
-      InitLaunch il{};
-      fill_init(il, U, B, lift, ld, p, seed, r);
-      il.y = ybuf[0];
-      il.gid = b->gid;
-      il.goff = b->goff;
-      if (r == 0) {
-        if (p->init == DECO_INIT_DUI) {
-          set_error("DUI is not available in batched solves");
-          return DECO_ERR_UNSUPPORTED;
-        }
-        if (p->init == DECO_INIT_IDI || p->init == DECO_INIT_IDI_HALF_UNIFORM) {
-          if ((rc = launch_idi_batch(U, 0.0, d_thresh, b->gid, b->goff, k0, k1, 0, h, side, st))) return rc;
-          kernels += 2;
-          il.mean = h;
-        }
-      } else {
-        il.init = DECO_INIT_MEAN;
-        il.mean_bits = rbz;
-      }
-      if ((rc = launch_init(il, st))) return rc;
-      kernels += 1;
-      if (vbuf) DECO_CUDA_TRY(cudaMemsetAsync(vbuf, 0, block_elems * sizeof(float), st));
-
-      Lane* L = nullptr;
-      for (auto& x : lanes) if (x->lift == lift) L = x.get();
-      const bool mom = vbuf != nullptr;
-      auto body = [&](int64_t* kc) -> int {
-        int cur = 0;
+    // Every round: set-up (step sizes, budgets), starting block, phase,
+    // rounding + cuts + per-graph records, scores + evolution -- all on the
+    // device, so the rounds are enqueued back to back and, when nothing in
+    // them allocates, captured as one CUDA graph and launched once.  The
+    // on-chip phase reads the round's longest budget from the device; the
+    // per-step kernels run the largest possible budget, t_hi steps, with the
+    // columns past their own budgets left unchanged (the same iterates).
+    bool can_capture = true;
+    for (auto& x : lanes) can_capture = can_capture && (x->S.ok || x->R.plan.col_slabs <= 1);
+    auto enqueue_rounds = [&](int64_t* kc) -> int {
+      for (int32_t r = 0; r < R; ++r) {
+        NvtxRange r_round("deco batch round");
+        const int32_t lift = pop->lifts[r % pop->n_lifts];
+        const int32_t C = B * lift;
+        k_pop_columns<<<1, 256, 0, st>>>(C, lift, per, P, d_e, d_T, alpha_cols, steps_cols, d_tmax + r,
+                                         d_hist_e + (size_t)r * P, d_hist_T + (size_t)r * P);
+        k_fill_round<<<1, 1, 0, st>>>(r, d_round);
+        cudaError_t ce = cudaSuccess;
+        // starting block of this round
+        InitLaunch il{};
+        fill_init(il, U, B, lift, ld, p, seed, r);
+        il.y = ybuf[0];
+        il.gid = b->gid;
+        il.goff = b->goff;
         int e2 = DECO_OK;
+        if (r == 0) {
+          if (p->init == DECO_INIT_IDI || p->init == DECO_INIT_IDI_HALF_UNIFORM) {
+            if ((e2 = launch_idi_batch(U, 0.0, d_thresh, b->gid, b->goff, k0, k1, 0, h, side, st))) return e2;
+            *kc += 2;
+            il.mean = h;
+          }
+        } else {
+          il.init = DECO_INIT_MEAN;
+          il.mean_bits = rbz;
+        }
+        if ((e2 = launch_init(il, st))) return e2;
+        *kc += 3;
+        if (vbuf) {
+          ce = cudaMemsetAsync(vbuf, 0, block_elems * sizeof(float), st);
+          if (ce != cudaSuccess) return cuda_fail(ce, "memset momentum");
+        }
+        Lane* L = nullptr;
+        for (auto& x : lanes) if (x->lift == lift) L = x.get();
+        const bool mom = vbuf != nullptr;
+        int cur = 0;
         if (L->S.ok) {
           // every graph's slabs in one on-chip launch, in place in ybuf[0]
           SlabParams sp{};
@@ -579,7 +684,8 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
           sp.xmode = L->S.lean ? 2 : 0;
           sp.lean = L->S.lean ? 1 : 0;
           sp.pairs = 1;   // row-pair form (256 BA graphs, FP32: 2.17 -> 1.83 s, same iterates)
-          sp.steps = tmax;
+          sp.steps = pop->t_hi;
+          sp.steps_dev = d_tmax + r;
           const float fac = p->objective == DECO_OBJ_MULTILINEAR01 ? 2.0f : 1.0f;
           sp.alpha = 0.0f;
           sp.afac = fac;
@@ -591,95 +697,80 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
           sp.max_own = L->S.max_own;
           sp.max_img_words = L->S.max_words;
           sp.flag = flag;
-          e2 = launch_slab(sp, L->S.n_items, p->precision, U->wmode, st);
-          if (kc) *kc += 1;
+          if ((e2 = launch_slab(sp, L->S.n_items, p->precision, U->wmode, st))) return e2;
+          *kc += 1;
         } else {
-          e2 = L->R.run(ybuf, cur, vbuf, tmax, p->objective, 0.0f, pop->momentum, alpha_cols, steps_cols, mom,
-                        false, flag, st, kc);
+          if ((e2 = L->R.run(ybuf, cur, vbuf, pop->t_hi, p->objective, 0.0f, pop->momentum, alpha_cols, steps_cols,
+                             mom, false, flag, st, kc)))
+            return e2;
         }
-        if (e2) return e2;
         if ((e2 = launch_pack(U, B, lift, ld, p->precision, ybuf[cur], zbits, st))) return e2;
-        cudaError_t ce = cudaMemsetAsync(cuts, 0, sizeof(int64_t) * (size_t)G * B, st);
+        ce = cudaMemsetAsync(cuts, 0, sizeof(int64_t) * (size_t)G * B, st);
         if (ce != cudaSuccess) return cuda_fail(ce, "memset cuts");
         dim3 grid((unsigned)((((int64_t)n + GCUT_ROWS - 1) / GCUT_ROWS + 7) / 8), (unsigned)W);
         k_cut_graphs<<<grid, 256, 0, st>>>(n, B, W, U->row_ptr, U->col_idx, U->wint, zbits, b->gid, cuts);
         k_argmax_graphs<<<G, 256, 0, st>>>(B, cuts, best_idx);
         k_record_graphs<<<(G + 127) / 128, 128, 0, st>>>(G, B, cuts, best_idx, d_round, rec_cut, rec_round, improved);
         k_extract_graphs<<<(n + 255) / 256, 256, 0, st>>>(n, W, zbits, b->gid, best_idx, improved, rbz, bz);
+        k_pop_close<<<1, 256, close_smem, st>>>(r, G, B, P, cuts, d_e, d_T, d_scores + (size_t)r * P,
+                                                d_rcuts ? d_rcuts + (size_t)r * G * B : nullptr, r + 1 < R ? 1 : 0,
+                                                k0, k1, (double)pop->e_lo, (double)pop->e_hi, pop->t_lo, pop->t_hi);
         ce = cudaGetLastError();
-        if (ce != cudaSuccess) return cuda_fail(ce, "batch bookkeeping");
-        if (kc) *kc += 5;
-        return DECO_OK;
-      };
-      // the phase length is part of the captured graph: capture again when the
-      // longest budget of this round differs from the captured one
-      if (L->uses >= 1 && L->R.plan.col_slabs <= 1) {
-        if (!L->exec || L->cap_steps != tmax) {
-          if (L->exec) cudaGraphExecDestroy(L->exec);
-          L->exec = nullptr;
-          L->cap_steps = tmax;
-          cudaGraph_t graph = nullptr;
-          DECO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          int64_t kc = 0;
-          const int brc = body(&kc);
-          cudaError_t ce = cudaStreamEndCapture(st, &graph);
-          if (brc) { if (graph) cudaGraphDestroy(graph); return brc; }
-          if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-          ce = cudaGraphInstantiate(&L->exec, graph, 0);
-          cudaGraphDestroy(graph);
-          if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        }
-        DECO_CUDA_TRY(cudaGraphLaunch(L->exec, st));
-        kernels += (int64_t)(L->S.ok || L->R.plan.kernel == KERNEL_ONCHIP ? 1 : tmax) + 5;
-      } else {
-        if ((rc = body(&kernels))) return rc;
+        if (ce != cudaSuccess) return cuda_fail(ce, "batch round");
+        *kc += 6;
       }
-      L->uses += 1;
-      edge_updates += U->nnz * (int64_t)C * tmax;   // every column is swept for the longest budget
-
-      // ---- rank, record, evolve (host, FP64)
-      DECO_CUDA_TRY(cudaMemcpyAsync(h_cuts.data(), cuts, sizeof(int64_t) * (size_t)G * B, cudaMemcpyDeviceToHost, st));
-      DECO_CUDA_TRY(cudaStreamSynchronize(st));
-      if (round_cuts) std::copy(h_cuts.begin(), h_cuts.end(), round_cuts + (size_t)r * G * B);
-      std::vector<long long> score(P, 0);
-      for (int32_t k = 0; k < P; ++k)
-        for (int32_t g = 0; g < G; ++g) {
-          long long m = LLONG_MIN;
-          for (int32_t j = k * per; j < (k + 1) * per; ++j) m = std::max<long long>(m, h_cuts[(size_t)g * B + j]);
-          score[k] += m;
-        }
-      if (round_scores) for (int32_t k = 0; k < P; ++k) round_scores[(size_t)r * P + k] = score[k];
-      if (r + 1 < pop->rounds) {
-        std::vector<int32_t> order(P);
-        for (int32_t k = 0; k < P; ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return score[a] > score[c]; });
-        const int32_t nkeep = P / 2;
-        std::vector<double> ne = e;
-        std::vector<int64_t> nT = T;
-        const int32_t nrep = P - nkeep;
-        for (int32_t j = 0; j < nrep; ++j) {
-          const int32_t victim = order[P - 1 - j];
-          const int32_t src = order[nkeep > 0 ? j % nkeep : 0];
-          uint32_t c[4] = {(uint32_t)j, (uint32_t)r, 1u, STREAM_EVOLVE};
-          philox_host(c, k0, k1);
-          const double kPi = 3.141592653589793;
-          const double eps = std::sqrt(-2.0 * std::log(u01_host(c[0]))) * std::cos(2.0 * kPi * u01_host(c[1]));
-          const double epsp = u01_host(c[2]);
-          ne[victim] = std::min(std::max(e[src] + 0.2 * eps, (double)pop->e_lo), (double)pop->e_hi);
-          const int64_t t = (int64_t)std::floor((double)T[src] * (1.0 + 0.2 * (2.0 * epsp - 1.0)));
-          nT[victim] = std::min<int64_t>(std::max<int64_t>(t, pop->t_lo), pop->t_hi);
-        }
-        e = ne;
-        T = nT;
-      }
+      return DECO_OK;
+    };
+    if (can_capture) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      DECO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int64_t kc = 0;
+      const int brc = enqueue_rounds(&kc);
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (brc) { if (graph) cudaGraphDestroy(graph); return brc; }
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+      ce = cudaGraphLaunch(exec, st);
+      cudaGraphExecDestroy(exec);   // released once the launch completes
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
+      kernels += kc;
+    } else if ((rc = enqueue_rounds(&kernels))) {
+      return rc;
     }
     DECO_CUDA_TRY(cudaEventRecord(ev1, st));
     int32_t hflag = 0;
+    std::vector<int32_t> h_tmax(R), h_T(P);
+    std::vector<double> h_e(P);
+    DECO_CUDA_TRY(cudaMemcpyAsync(h_tmax.data(), d_tmax, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, st));
+    DECO_CUDA_TRY(cudaMemcpyAsync(h_e.data(), d_e, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+    DECO_CUDA_TRY(cudaMemcpyAsync(h_T.data(), d_T, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
+    std::vector<long long> h_scores((size_t)R * P);
+    DECO_CUDA_TRY(cudaMemcpyAsync(h_scores.data(), d_scores, sizeof(long long) * (size_t)R * P,
+                                  cudaMemcpyDeviceToHost, st));
+    if (round_cuts)
+      DECO_CUDA_TRY(cudaMemcpyAsync(round_cuts, d_rcuts, sizeof(int64_t) * (size_t)R * G * B, cudaMemcpyDeviceToHost,
+                                    st));
     DECO_CUDA_TRY(cudaMemcpyAsync(hrec.data(), rec_cut, sizeof(long long) * G, cudaMemcpyDeviceToHost, st));
     DECO_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     if (assignment) DECO_CUDA_TRY(cudaMemcpyAsync(assignment, bz, (size_t)n, cudaMemcpyDeviceToHost, st));
     DECO_CUDA_TRY(cudaStreamSynchronize(st));
     DECO_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+    if (round_scores) for (size_t i = 0; i < (size_t)R * P; ++i) round_scores[i] = h_scores[i];
+    for (int32_t k = 0; k < P; ++k) {
+      e[k] = h_e[k];
+      T[k] = h_T[k];
+    }
+    // every column is swept for the round's longest budget (the on-chip
+    // phase), or for t_hi steps (the per-step kernels)
+    for (int32_t r = 0; r < R; ++r) {
+      const int32_t lift = pop->lifts[r % pop->n_lifts];
+      bool onchip = false;
+      for (auto& x : lanes) if (x->lift == lift) onchip = x->S.ok;
+      edge_updates += U->nnz * (int64_t)B * lift * (onchip ? h_tmax[r] : pop->t_hi);
+    }
     if (hflag & 2) { set_error("a bounded device wait of the on-chip or dense kernel gave up"); return DECO_ERR_TIMEOUT; }
     if (hflag) { set_error("a non-finite value appeared in the iterate"); return DECO_ERR_NONFINITE; }
   }

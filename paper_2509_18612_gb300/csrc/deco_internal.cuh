@@ -59,21 +59,30 @@ struct SlabImage {
   int32_t max_words = 0;             // largest part in 32-bit words
 };
 
-// Sliced copy of the CSR for the pipelined per-step kernel (step_sell.cu),
-// built once per slice height and kept with the graph: rows sorted by degree
-// (largest first, ties by index) in slices of ng rows; slice s holds
-// width[s] entries per row, entry k of its row i at off[s] + k * ng + i
-// (column index, with the sign of a +-1 weight in bit 31; 0xFFFFFFFF past the
-// row's degree).
-struct SellImage {
-  int ng = 0;
-  int32_t nslices = 0;
-  std::vector<int32_t> width;   // host copy of the widths
-  int64_t* off = nullptr;       // device, nslices + 1
-  int2* rows = nullptr;         // device, nslices * ng: (row, degree); (-1, 0) past the last row
-  int32_t* width_d = nullptr;   // device, nslices
-  uint32_t* idx = nullptr;      // device entries
-  float* w = nullptr;           // device weights in the same layout (general weights only)
+// Per-warp record streams of the pipelined per-step kernel (step_stream.cu),
+// built once per (slice height, entries per item, warp count, weights) and
+// kept with the graph: rows sorted by degree in slices of ng rows, slice s
+// given to warp s mod nw, each warp's items one contiguous run of rw-word
+// records starting at record soff[warp].
+struct StreamImage {
+  int ng = 0, maxe = 0, nw = 0;
+  bool gen = false;             // records carry general weights
+  int32_t rw = 0;               // words per record
+  int64_t records = 0;
+  uint32_t* rec = nullptr;      // device records
+  int32_t* soff = nullptr;      // device, nw + 1
+};
+
+// Launch shape of the pipelined per-step kernel.
+struct StreamShape {
+  int G = 16;          // lanes per row segment (32 / slice height)
+  int maxe = 16;       // entries per item
+  int stages = 3;      // shared-memory gather stages per warp
+  int wpb = 8;         // warps per block
+  int blocks = 0;      // grid: the blocks resident at once
+  int nw = 0;          // blocks * wpb
+  bool weighted = false, gen = false, mixed = false;
+  bool hints = false;  // records and new rows evict-first in L2
 };
 
 // The opaque handle of the ABI.
@@ -91,7 +100,7 @@ struct deco_graph {
   std::vector<int32_t> h_col;       // host copy of the device edge order
   std::vector<float> h_w;           // host copy of the device-order weights (or empty)
   std::vector<SlabImage> images;    // on-chip CSR images, one per cluster size used
-  std::deque<SellImage> sells;      // sliced CSR copies of the pipelined step kernel, one per slice height
+  std::deque<StreamImage> streams;  // record streams of the pipelined step kernel, one per launch shape
                                     // (a deque: phase plans keep pointers to them while others are added)
   __nv_bfloat16* dense = nullptr;   // dense BF16 copy of A for the tensor-core kernel (built on first use)
   int32_t dense_ld = 0;             // its row stride, round_up(n, 128)
@@ -171,16 +180,15 @@ struct StepLaunch {
   int32_t* flag;
 };
 int launch_step_global(const StepLaunch& s, cudaStream_t st);
-// The pipelined form of the same step (bit-identical iterates): `im` from
-// sell_image(g, 32 / sell_group_lanes(C, precision)); maxe entries per part,
-// `stages` shared-memory stages, wpb warps per block; mixed_add: BF16 sums
-// of unit-weight rows with the mixed-precision add instruction (same result).
-int launch_step_sell(const StepLaunch& s, const SellImage& im, int maxe, int stages, int wpb, bool mixed_add,
-                     cudaStream_t st);
-int sell_group_lanes(int32_t C, int prec);
-int sell_image(deco_graph* g, int ng, const SellImage** out);
-void free_sell_image(SellImage& im);
-size_t sell_smem_bytes(int32_t C, int prec, int maxe, int stages, int wpb, bool mom, bool weighted);
+// The pipelined form of the same step (bit-identical iterates): the shape
+// for a block of C columns (stream_shape, which also sizes the grid), the
+// graph's record streams for that shape (stream_image), one launch.
+int stream_group_lanes(int32_t C, int prec);
+int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weighted, bool gen, bool mixed,
+                 bool hints, StreamShape* out);
+int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out);
+void free_stream_image(StreamImage& im);
+int launch_step_stream(const StepLaunch& s, const StreamImage& im, const StreamShape& sh, cudaStream_t st);
 // row-major n x ld (columns < C)  <->  S dense slabs of n x w (column c in slab c / w)
 int launch_slab_layout(int32_t n, int32_t ld, int32_t C, int32_t w, int32_t S, size_t esz, const void* src,
                        void* dst, bool to_slabs, cudaStream_t st);

@@ -44,7 +44,7 @@ double idi_threshold(const deco_graph* g, float beta) {
 static void free_graph(deco_graph* g) {
   if (!g) return;
   for (auto& im : g->images) cudaFree(im.data);
-  for (auto& im : g->sells) free_sell_image(im);
+  for (auto& im : g->streams) free_stream_image(im);
   cudaFree(g->dense);
   cudaFree(g->row_ptr);
   cudaFree(g->col_idx);

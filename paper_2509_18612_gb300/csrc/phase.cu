@@ -63,7 +63,8 @@ static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int wa
 
 bool valid_selector(int kernel) {
   const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
-  const int s = (kernel >> 16) & 0xF;
+  const int s = (kernel >> 16) & 0x7;
+  const int l2hints = (kernel >> 19) & 1;
   const int lean = (kernel >> 20) & 1;
   const int pairs = (kernel >> 21) & 1;
   const int pipe = (kernel >> 22) & 1;
@@ -71,9 +72,11 @@ bool valid_selector(int kernel) {
   const int mixed = (kernel >> 30) & 1;
   if (kernel & ~0x7FFFFFFF) return false;
   if (mixed && !pipe) return false;
+  if (l2hints && !pipe) return false;
+  if (pipe && ((pipe_shape >> 2) & 3) == 3 && (pipe_shape & 3) > 1 && (pipe_shape & 3) != 0)
+    return false;   // the register form takes 8 or 16 entries
   if (pipe && kind != DECO_KERNEL_GLOBAL) return false;
   if (!pipe && pipe_shape) return false;
-  if (pipe && ((pipe_shape >> 2) & 3) == 3) return false;   // stage code 3 is not defined
   if (lean && kind != DECO_KERNEL_ONCHIP) return false;
   if (pairs && kind != DECO_KERNEL_ONCHIP) return false;
   if (lean && x == 1) return false;   // the lean form exchanges through L2
@@ -162,7 +165,8 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const int want_k = (force >> 8) & 0xF;
   const int want_t = (force >> 12) & 0x3;
   const int want_x = (force >> 14) & 0x3;
-  const int want_s = (force >> 16) & 0xF;
+  const int want_s = (force >> 16) & 0x7;
+  const bool want_hints = ((force >> 19) & 1) != 0;
   const bool want_lean = ((force >> 20) & 1) != 0;
   const bool want_pipe = ((force >> 22) & 1) != 0;
   const int pipe_e = (force >> 23) & 3, pipe_s = (force >> 25) & 3, pipe_w = (force >> 27) & 7;
@@ -181,15 +185,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   plan->lean = want_lean;
   plan->pairs = want_pairs;
   if (force == DECO_KERNEL_GLOBAL) {
-    if (want_pipe) {
-      static const int entries[4] = {16, 8, 24, 32};
-      static const int stages[3] = {3, 2, 4};
-      plan->pipe = true;
-      plan->pipe_maxe = entries[pipe_e];
-      plan->pipe_stages = stages[pipe_s];
-      plan->pipe_wpb = pipe_w;
-      plan->pipe_mixed = pipe_mix;
-    }
+    if (want_pipe) plan->pipe = true;
     if (want_s) {
       // column slabs of width w, run one after another in a slab-major copy
       const int S = 1 << want_s;
@@ -202,22 +198,13 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
       plan->slab_w = w;
     }
     if (plan->pipe) {
-      // warps per block: as many as the shared memory holds (at most 8), or the given count
+      static const int entries[4] = {16, 8, 24, 32};
+      static const int stages[4] = {3, 2, 4, 0};   // 0: the register form
       const int cols = plan->col_slabs > 1 ? plan->slab_w : C;
-      const int max_smem = slab_max_smem();
-      int wpb = plan->pipe_wpb;
-      if (!wpb) {
-        wpb = 8;
-        while (wpb > 1 && sell_smem_bytes(cols, prec, plan->pipe_maxe, plan->pipe_stages, wpb, true, true) >
-                              (size_t)max_smem)
-          --wpb;
-      }
-      if (sell_smem_bytes(cols, prec, plan->pipe_maxe, plan->pipe_stages, wpb, true, true) > (size_t)max_smem) {
-        set_error("the pipelined step kernel does not fit %d warps of %d entries x %d stages", wpb,
-                  plan->pipe_maxe, plan->pipe_stages);
-        return DECO_ERR_UNSUPPORTED;
-      }
-      plan->pipe_wpb = wpb;
+      const bool weighted = g->wmode != W_UNIT, gen = g->wmode == W_GENERAL;
+      int rc = stream_shape(cols, prec, entries[pipe_e], stages[pipe_s], pipe_w, weighted, gen, pipe_mix, want_hints,
+                            &plan->stream);
+      if (rc) return rc;
     }
     return DECO_OK;
   }
@@ -299,9 +286,8 @@ int PhaseRunner::prepare(const deco_graph* g_, int32_t C_, int32_t ld_, int prec
   }
   if (plan.kernel == KERNEL_GLOBAL && plan.pipe) {
     std::lock_guard<std::mutex> lock(g_image_mutex);
-    // the sliced copy lives with the graph, like the on-chip CSR images
-    const int cols = plan.col_slabs > 1 ? plan.slab_w : C;
-    return sell_image(const_cast<deco_graph*>(g), 32 / sell_group_lanes(cols, prec), &plan.sell);
+    // the record streams live with the graph, like the on-chip CSR images
+    return stream_image(const_cast<deco_graph*>(g), plan.stream, &plan.rec);
   }
   if (plan.kernel != KERNEL_ONCHIP) return DECO_OK;
   {
@@ -418,8 +404,7 @@ int PhaseRunner::run(void* y[2], int& cur, float* v, int32_t steps, int objectiv
   }
   // one step: the pipelined form where planned, else the lane-group form
   auto step_launch = [&](const StepLaunch& s, cudaStream_t stream) -> int {
-    if (plan.pipe)
-      return launch_step_sell(s, *plan.sell, plan.pipe_maxe, plan.pipe_stages, plan.pipe_wpb, plan.pipe_mixed, stream);
+    if (plan.pipe) return launch_step_stream(s, *plan.rec, plan.stream, stream);
     return launch_step_global(s, stream);
   };
   StepLaunch sl{};

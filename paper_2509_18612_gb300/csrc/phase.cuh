@@ -19,12 +19,9 @@ struct PhasePlan {
   bool pairs = false;            // on-chip kernel: row-pair form (a half-warp per row)
   int col_slabs = 1;             // global kernel: column slabs run one after another (slab-major)
   int slab_w = 0;                // their width
-  bool pipe = false;             // global kernel: the pipelined form (step_sell.cu)
-  int pipe_maxe = 16;            // its entries per stage, stages and warps per block
-  int pipe_stages = 3;
-  int pipe_wpb = 0;              // 0: as many as fit (at most 8)
-  bool pipe_mixed = false;       // BF16 unit-weight sums with the mixed-precision add
-  const SellImage* sell = nullptr;   // its sliced CSR copy (owned by the graph)
+  bool pipe = false;             // global kernel: the pipelined form (step_stream.cu)
+  StreamShape stream;            // its launch shape
+  const StreamImage* rec = nullptr;   // its record streams (owned by the graph)
   int items = 0;                 // column slabs
   int32_t max_own = 0, max_img_words = 0;
   SlabImage image;               // on-chip CSR image (owned by the graph)

@@ -349,7 +349,10 @@ __global__ void __launch_bounds__(NT, 1) k_slab(SlabParams P) {
   }
   cluster.sync();   // every replica is loaded (and the barrier initialised) before any exchange
 
-  for (int t = 0; t < P.steps; ++t) {
+  // a device-side bound (the longest budget of a population round) keeps the
+  // launch as short as the round, inside a captured graph as well
+  const int nsteps = P.steps_dev ? min(P.steps, __ldg(P.steps_dev)) : P.steps;
+  for (int t = 0; t < nsteps; ++t) {
     if constexpr (PAIR) {
       // two rows per warp, one per half-warp (the second half idles on the
       // last row of an odd range)

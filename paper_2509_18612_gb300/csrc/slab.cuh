@@ -40,6 +40,7 @@ struct SlabParams {
   int32_t threads;             // CTA size: 512 or 1024
   int32_t xmode;               // exchange between the cluster's CTAs: 1 DSMEM, 2 L2 (k > 1)
   int32_t steps;               // steps of this launch
+  const int32_t* steps_dev;    // device value bounding the steps (min with `steps`), or null
   float alpha;                 // scalar step size with the objective factor applied
   float afac;                  // objective factor applied to alpha_cols
   float mu;
