@@ -151,12 +151,9 @@ typedef enum deco_status {
  * S - 1 items ahead, and sums an item's rows in CSR order from shared memory.
  * Same iterates as the other forms.  Its shape:
  *   DECO_KERNEL_PIPE_ENTRIES(e)  entries of a row per item: e = 0: 16,
- *                                1: 8, 2: 24, 3: 32 (longer rows go in parts)
+ *                                1: 8, 2: 24, 3: 12 (longer rows go in parts)
  *   DECO_KERNEL_PIPE_STAGES(s)   shared-memory stages per warp: s = 0: 3,
- *                                1: 2, 2: 4; s = 3: the register form (no
- *                                gather stages: each lane loads its 16 bytes
- *                                of the item's rows into registers; 8 or 16
- *                                entries only), for L2-resident column slabs
+ *                                1: 2, 2: 4
  *   DECO_KERNEL_PIPE_WARPS(w)    warps per block: w = 0: as many as fit
  *                                (at most 8), 1..7: w */
 #define DECO_KERNEL_PIPELINED (1 << 22)

@@ -49,17 +49,17 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
 
   std::vector<int> cands = {DECO_KERNEL_GLOBAL};
   for (int s = 1; s <= 4; ++s) cands.push_back(DECO_KERNEL_GLOBAL | (s << 16));   // 2..16 column slabs
-  // the pipelined per-step form (record streams, cp.async stages): 8 / 16 /
-  // 24 entries per item, 2 or 3 stages, the mixed-precision BF16 add, with and
-  // without the L2 eviction priorities, on the whole block and on 2 or 4
-  // column slabs
-  for (int s = 0; s <= 2; ++s)
-    for (int e : {1, 0, 2})
-      for (int st : {1, 0})
-        for (int h : {0, 1})
-          cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(e) |
-                          DECO_KERNEL_PIPE_STAGES(st) | DECO_KERNEL_PIPE_MIXED_ADD |
-                          (h ? DECO_KERNEL_PIPE_L2_HINTS : 0));
+  // the pipelined per-step form (record streams, cp.async stages), with the
+  // mixed-precision BF16 add: 8 / 12 / 16 entries per item and 2 stages, or 8
+  // entries and 3 stages, on the whole block and on 2 or 4 column slabs (the
+  // shapes that measured competitive on a 10^6-node graph)
+  for (int s = 0; s <= 2; ++s) {
+    for (int e : {1, 3, 0})
+      cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(e) |
+                      DECO_KERNEL_PIPE_STAGES(1) | DECO_KERNEL_PIPE_MIXED_ADD);
+    cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(1) |
+                    DECO_KERNEL_PIPE_STAGES(0) | DECO_KERNEL_PIPE_MIXED_ADD);
+  }
   for (int k = 1; k <= 8; k *= 2)
     for (int t = 1; t <= 2; ++t)
       for (int x = 1; x <= 2; ++x) {

@@ -81,7 +81,8 @@ struct StreamShape {
   int wpb = 8;         // warps per block
   int blocks = 0;      // grid: the blocks resident at once
   int nw = 0;          // blocks * wpb
-  bool weighted = false, gen = false, mixed = false;
+  bool weighted = false, gen = false;
+  int acc = 0;         // BF16 unit-weight sums: 0 widen + add, 1 mixed-precision add
   bool hints = false;  // records and new rows evict-first in L2
 };
 

@@ -73,8 +73,7 @@ bool valid_selector(int kernel) {
   if (kernel & ~0x7FFFFFFF) return false;
   if (mixed && !pipe) return false;
   if (l2hints && !pipe) return false;
-  if (pipe && ((pipe_shape >> 2) & 3) == 3 && (pipe_shape & 3) > 1 && (pipe_shape & 3) != 0)
-    return false;   // the register form takes 8 or 16 entries
+  if (pipe && ((pipe_shape >> 2) & 3) == 3) return false;   // stage code 3 is not defined
   if (pipe && kind != DECO_KERNEL_GLOBAL) return false;
   if (!pipe && pipe_shape) return false;
   if (lean && kind != DECO_KERNEL_ONCHIP) return false;
@@ -198,8 +197,8 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
       plan->slab_w = w;
     }
     if (plan->pipe) {
-      static const int entries[4] = {16, 8, 24, 32};
-      static const int stages[4] = {3, 2, 4, 0};   // 0: the register form
+      static const int entries[4] = {16, 8, 24, 12};
+      static const int stages[3] = {3, 2, 4};
       const int cols = plan->col_slabs > 1 ? plan->slab_w : C;
       const bool weighted = g->wmode != W_UNIT, gen = g->wmode == W_GENERAL;
       int rc = stream_shape(cols, prec, entries[pipe_e], stages[pipe_s], pipe_w, weighted, gen, pipe_mix, want_hints,

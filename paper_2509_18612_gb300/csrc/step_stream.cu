@@ -131,7 +131,9 @@ struct Pos {
   }
 };
 
-template <int PREC, int G, bool WT, bool MIX>
+// ACC: how the BF16 rows of unit-weight graphs are summed (the same value
+// either way): 0 widened and added in FP32, 1 with the mixed-precision add.
+template <int PREC, int G, bool WT, int ACC>
 __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using V = VecT<PREC>;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ Str
       for (int k = 0; k < kmax; ++k) {
         if (k < cnt) {
           const uint4 q = *reinterpret_cast<const uint4*>(gp + (size_t)k * W);
-          if (MIX && PREC == DECO_PREC_BF16 && !WT) {
+          if (ACC == 1 && PREC == DECO_PREC_BF16 && !WT) {
             add_bf16x8(*reinterpret_cast<float(*)[8]>(acc), q);
           } else {
             float val[VN];
@@ -321,207 +323,27 @@ __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ Str
   if (bad && a.flag) atomicExch(a.flag, 1);
 }
 
-// Register form of the same kernel (stages code 3): the records still come
-// through the shared-memory ring, three items ahead, but every lane loads its
-// 16 bytes of the item's neighbour rows straight into registers (KMAX =
-// maxe of them), sums them and updates its rows; no gather staging, so the
-// registers, not shared memory, set the occupancy.  Meant for column slabs
-// that stay in L2, whose short latency a full SM of warps hides.
-template <int PREC, int G, bool WT, bool MIX, int KMAX>
-__global__ void __launch_bounds__(256, KMAX <= 8 ? 3 : 2) k_step_stream_reg(const __grid_constant__ StreamArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  using V = VecT<PREC>;
-  constexpr int NG = 32 / G;
-  constexpr int VN = V::N;
-  constexpr int E0 = 1 + 2 * NG;
-  constexpr int RR = 4;   // record ring: fetched three items ahead
-  constexpr size_t ESZ = PREC == DECO_PREC_BF16 ? 2 : 4;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int g = lane / G, j = lane % G;
-  const int RW = a.rw;
-  const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
-  const int32_t i0 = __ldg(a.soff + warp);
-  const int32_t m = __ldg(a.soff + warp + 1) - i0;
-  if (m == 0) return;
-  const int64_t total = (int64_t)m * a.ncc;
-  const uint32_t rec_bytes = (uint32_t)RW * 4u;
-  unsigned char* const wsm = smem + (size_t)wib * RR * rec_bytes;
-  const uint32_t wsm_s = smem_u32(wsm);
-  const uint32_t* const ring = reinterpret_cast<const uint32_t*>(wsm);
-  const size_t row_bytes = (size_t)a.ld * ESZ;
-  const uint32_t* const wrec = a.rec + (size_t)i0 * RW;
-  const bool mom = a.mom != 0, lap = a.lap != 0;
-  const uint64_t pol_first = a.hints ? policy_evict_first() : 0;
-
-  float acc[VN];
-#pragma unroll
-  for (int k = 0; k < VN; ++k) acc[k] = 0.0f;
-  bool bad = false;
-
-  Pos pf{0, 0}, pc{0, 0};
-  int sf = 0, sc = 0;
-  for (int64_t t = -(RR - 1); t < total; ++t) {
-    if (t + RR - 1 < total) {
-      for (int l = lane; l * 4 < RW; l += 32) {
-        const uint32_t dst = wsm_s + (uint32_t)sf * rec_bytes + (uint32_t)l * 16u;
-        const uint32_t* src = wrec + (size_t)pf.r * RW + l * 4;
-        if (a.hints) cp16_hint(dst, src, pol_first);
-        else cp16(dst, src);
-      }
-      pf.next(m);
-      if (++sf == RR) sf = 0;
-    }
-    cp_commit();
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // the record of item t has landed
-    __syncwarp();
-    if (t >= 0) {
-      const uint32_t* rc = ring + (size_t)sc * RW;
-      const int c0 = (pc.cc * G + j) * VN;
-      const bool col_ok = c0 < a.C;
-      const int kmax = (int)rc[0];
-      const int row = (int)rc[1 + g];
-      const uint32_t info = rc[1 + NG + g];
-      const int cnt = (int)(info & 0xFFFFu);
-      const bool last = ((info >> 17) & 1u) != 0;
-      const char* yb = static_cast<const char*>(a.yin) + (size_t)c0 * ESZ;
-      // loads: the item's neighbour rows, then (last part) the own row and momentum
-      // (the unrolled loops leave at the item's width instead of issuing
-      // predicated slots up to KMAX)
-      uint4 buf[KMAX];
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= kmax) break;
-        if (k < cnt && col_ok) {
-          const uint32_t e = rc[E0 + k * NG + g];
-          buf[k] = __ldg(reinterpret_cast<const uint4*>(yb + (size_t)(e & 0x7FFFFFFFu) * row_bytes));
-        }
-      }
-      uint4 yq = make_uint4(0, 0, 0, 0);
-      float vv[VN];
-#pragma unroll
-      for (int k = 0; k < VN; ++k) vv[k] = 0.0f;
-      const bool upd = last && row >= 0 && col_ok;
-      if (upd) {
-        yq = __ldg(reinterpret_cast<const uint4*>(yb + (size_t)row * row_bytes));
-        if (mom) {
-          const float4* vrow = reinterpret_cast<const float4*>(a.v + (size_t)row * a.ld + c0);
-#pragma unroll
-          for (int h = 0; h < VN / 4; ++h) {
-            const float4 q = vrow[h];
-            vv[4 * h] = q.x; vv[4 * h + 1] = q.y; vv[4 * h + 2] = q.z; vv[4 * h + 3] = q.w;
-          }
-        }
-      }
-      if (info & 0x10000u) {
-#pragma unroll
-        for (int k = 0; k < VN; ++k) acc[k] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= kmax) break;
-        if (k < cnt) {
-          if (MIX && PREC == DECO_PREC_BF16 && !WT) {
-            add_bf16x8(*reinterpret_cast<float(*)[8]>(acc), buf[k]);
-          } else {
-            float val[VN];
-            unpack<PREC>(buf[k], val);
-            if (WT) {
-              const uint32_t e = rc[E0 + k * NG + g];
-              const float wt = a.gen ? __uint_as_float(rc[E0 + a.maxe * NG + k * NG + g])
-                                     : ((e & 0x80000000u) ? -1.0f : 1.0f);
-#pragma unroll
-              for (int h = 0; h < VN; ++h) acc[h] = fmaf(wt, val[h], acc[h]);
-            } else {
-#pragma unroll
-              for (int h = 0; h < VN; ++h) acc[h] = acc[h] + val[h];
-            }
-          }
-        }
-      }
-      if (upd) {
-        float y[VN], out[VN];
-        unpack<PREC>(yq, y);
-        const float dr = lap ? __ldg(a.dnet + row) : 0.0f;
-#pragma unroll
-        for (int k = 0; k < VN; ++k) {
-          const float grad = lap ? fmaf(dr, y[k], -acc[k]) : -acc[k];
-          const float step = mom ? fmaf(a.mu, vv[k], grad) : grad;
-          // per-column step size and budget (L1-cached), as in k_step_global
-          const int c = c0 + k;
-          const float alpha = a.alpha_cols ? a.afac * __ldg(a.alpha_cols + (c < a.C ? c : 0)) : a.alpha_eff;
-          const bool active = (c < a.C) && (!a.steps_cols || a.t < __ldg(a.steps_cols + c));
-          float yn = fmaf(alpha, step, y[k]);
-          if (active && !isfinite(yn)) bad = true;
-          yn = fminf(fmaxf(yn, -1.0f), 1.0f);
-          out[k] = active ? yn : y[k];
-          if (mom && active) vv[k] = step;
-        }
-        const size_t base = (size_t)row * a.ld + c0;
-        if (c0 + VN <= a.C) {
-          if (a.hints) {
-            uint4 q;
-            if (PREC == DECO_PREC_FP32) {
-              q = make_uint4(__float_as_uint(out[0]), __float_as_uint(out[1]), __float_as_uint(out[2]),
-                             __float_as_uint(out[3]));
-            } else {
-              q = make_uint4(pack_bf16x2(out[0], out[1]), pack_bf16x2(out[2], out[3]), pack_bf16x2(out[4], out[5]),
-                             pack_bf16x2(out[6], out[7]));
-            }
-            st_hint_v4(static_cast<char*>(a.yout) + base * ESZ, q, pol_first);
-          } else {
-            V::store(a.yout, base, out);
-          }
-          if (mom) {
-#pragma unroll
-            for (int k = 0; k < VN; k += 4)
-              *reinterpret_cast<float4*>(a.v + base + k) = make_float4(vv[k], vv[k + 1], vv[k + 2], vv[k + 3]);
-          }
-        } else {
-          for (int k = 0; k < VN && c0 + k < a.C; ++k) {
-            if (PREC == DECO_PREC_FP32) static_cast<float*>(a.yout)[base + k] = out[k];
-            else static_cast<__nv_bfloat16*>(a.yout)[base + k] = __float2bfloat16_rn(out[k]);
-            if (mom) a.v[base + k] = vv[k];
-          }
-        }
-      }
-      pc.next(m);
-      if (++sc == RR) sc = 0;
-    }
-    __syncwarp();   // every lane is done with the record before its slot is refilled
-  }
-  if (bad && a.flag) atomicExch(a.flag, 1);
-}
-
-template <int PREC, int G, bool WT, bool MIX>
-struct Kern {
-  static void* fn(bool reg, int maxe) {
-    if (!reg) return reinterpret_cast<void*>(k_step_stream<PREC, G, WT, MIX>);
-    return maxe <= 8 ? reinterpret_cast<void*>(k_step_stream_reg<PREC, G, WT, MIX, 8>)
-                     : reinterpret_cast<void*>(k_step_stream_reg<PREC, G, WT, MIX, 16>);
-  }
-};
-
 template <int PREC, int G>
-void* pick_wt(bool wt, bool mix, bool reg, int maxe) {
-  if (wt) return Kern<PREC, G, true, false>::fn(reg, maxe);
-  if (PREC == DECO_PREC_BF16 && mix) return Kern<PREC, G, false, true>::fn(reg, maxe);
-  return Kern<PREC, G, false, false>::fn(reg, maxe);
+void* pick_wt(bool wt, int acc) {
+  if (wt) return reinterpret_cast<void*>(k_step_stream<PREC, G, true, 0>);
+  if (PREC == DECO_PREC_BF16 && acc == 1) return reinterpret_cast<void*>(k_step_stream<PREC, G, false, 1>);
+  return reinterpret_cast<void*>(k_step_stream<PREC, G, false, 0>);
 }
 
-void* pick_kernel(int prec, int G, bool wt, bool mix, bool reg, int maxe) {
+void* pick_kernel(int prec, int G, bool wt, int acc) {
   if (prec == DECO_PREC_BF16) {
     switch (G) {
-      case 4: return pick_wt<DECO_PREC_BF16, 4>(wt, mix, reg, maxe);
-      case 8: return pick_wt<DECO_PREC_BF16, 8>(wt, mix, reg, maxe);
-      case 16: return pick_wt<DECO_PREC_BF16, 16>(wt, mix, reg, maxe);
-      default: return pick_wt<DECO_PREC_BF16, 32>(wt, mix, reg, maxe);
+      case 4: return pick_wt<DECO_PREC_BF16, 4>(wt, acc);
+      case 8: return pick_wt<DECO_PREC_BF16, 8>(wt, acc);
+      case 16: return pick_wt<DECO_PREC_BF16, 16>(wt, acc);
+      default: return pick_wt<DECO_PREC_BF16, 32>(wt, acc);
     }
   }
   switch (G) {
-    case 4: return pick_wt<DECO_PREC_FP32, 4>(wt, false, reg, maxe);
-    case 8: return pick_wt<DECO_PREC_FP32, 8>(wt, false, reg, maxe);
-    case 16: return pick_wt<DECO_PREC_FP32, 16>(wt, false, reg, maxe);
-    default: return pick_wt<DECO_PREC_FP32, 32>(wt, false, reg, maxe);
+    case 4: return pick_wt<DECO_PREC_FP32, 4>(wt, 0);
+    case 8: return pick_wt<DECO_PREC_FP32, 8>(wt, 0);
+    case 16: return pick_wt<DECO_PREC_FP32, 16>(wt, 0);
+    default: return pick_wt<DECO_PREC_FP32, 32>(wt, 0);
   }
 }
 
@@ -531,12 +353,6 @@ void stream_sizes(int G, int prec, int maxe, int stages, bool mom, bool gen, int
   const int NG = 32 / G, VN = prec == DECO_PREC_BF16 ? 8 : 4, W = 16 * G;
   const int words = 1 + 2 * NG + maxe * NG * (gen ? 2 : 1);
   *rw = (words + 3) / 4 * 4;
-  if (stages == 0) {   // the register form: a ring of 4 records, no stages
-    *group = 0;
-    *stage = 0;
-    *per_warp = (size_t)4 * *rw * 4;
-    return;
-  }
   *group = (uint32_t)(maxe + 1) * W + (mom ? (uint32_t)(G * VN * 4) : 0u);
   *stage = (uint32_t)NG * *group;
   *per_warp = (size_t)2 * stages * *rw * 4 + (size_t)stages * *stage;
@@ -556,8 +372,7 @@ int stream_group_lanes(int32_t C, int prec) {
 
 int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weighted, bool gen, bool mixed,
                  bool hints, StreamShape* out) {
-  if (maxe < 1 || maxe > 0xFFFF || (stages != 0 && stages < 2) || stages > 4 || wpb < 0 || wpb > 8 ||
-      (stages == 0 && maxe > 16)) {
+  if (maxe < 1 || maxe > 0xFFFF || stages < 2 || stages > 4 || wpb < 0 || wpb > 8) {
     set_error("pipelined step: bad shape (entries=%d, stages=%d, warps=%d)", maxe, stages, wpb);
     return DECO_ERR_ARG;
   }
@@ -567,7 +382,7 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
   sh.stages = stages;
   sh.gen = gen;
   sh.weighted = weighted;
-  sh.mixed = mixed && prec == DECO_PREC_BF16 && !weighted;
+  sh.acc = (mixed && prec == DECO_PREC_BF16 && !weighted) ? 1 : 0;
   sh.hints = hints;
   int32_t rw;
   uint32_t group, stage;
@@ -590,7 +405,7 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
   }
   sh.wpb = wpb;
   // grid: as many blocks as are resident at once (without momentum slots)
-  void* fn = pick_kernel(prec, sh.G, weighted, sh.mixed, stages == 0, maxe);
+  void* fn = pick_kernel(prec, sh.G, weighted, sh.acc);
   const size_t smem = per_warp * wpb;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e != cudaSuccess) return cuda_fail(e, "pipelined step shared memory");
@@ -741,7 +556,7 @@ int launch_step_stream(const StepLaunch& s, const StreamImage& im, const StreamS
     set_error("pipelined step: %zu bytes of shared memory exceed the %d available", smem, max_smem);
     return DECO_ERR_UNSUPPORTED;
   }
-  void* fn = pick_kernel(s.precision, sh.G, sh.weighted, sh.mixed, sh.stages == 0, sh.maxe);
+  void* fn = pick_kernel(s.precision, sh.G, sh.weighted, sh.acc);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)sh.blocks), dim3(32 * sh.wpb), args, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "k_step_stream launch");

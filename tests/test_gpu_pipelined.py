@@ -115,9 +115,9 @@ def test_pipelined_step_bitwise_equals_lane_groups(name, precision, C, ld):
 @pytest.mark.parametrize("warps", [0, 1, 3])
 def test_pipelined_shapes_bitwise(entries, stages, warps):
     # every entries-per-item / stage-count / block shape on the graph with
-    # rows of up to 300 entries (up to 38 parts of 8); stage code 3 is the
-    # register form, which takes 8 or 16 entries only
-    if stages == 3 and entries in (2, 3):
+    # rows of up to 300 entries (up to 38 parts of 8); stage code 3 is not
+    # defined and is refused
+    if stages == 3:
         with pytest.raises(deco.DecoError):
             deco.deco_run_phase(deco.graph_from(GRAPHS["er800"]()), 64, 64, torch.zeros(800, 64, device=DEV), None,
                                 1, deco.step_args(), PIPE | deco.DECO_KERNEL_PIPE_ENTRIES(entries)
@@ -203,44 +203,3 @@ def test_pipelined_mixed_precision_add_bitwise(name, C, ld):
     _same(ref, got, y, C)
 
 
-
-REG = PIPE | deco.DECO_KERNEL_PIPE_STAGES(3)
-
-
-@pytest.mark.parametrize("name", list(GRAPHS))
-@pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
-@pytest.mark.parametrize("C,ld", [(128, 128), (203, 256), (24, 64), (520, 576)])
-@pytest.mark.parametrize("entries", [0, 1])
-def test_register_form_bitwise_equals_lane_groups(name, precision, C, ld, entries):
-    # the register form of the pipelined kernel (records through shared
-    # memory, gathers into registers), 16 or 8 entries per item
-    g = GRAPHS[name]()
-    G = deco.graph_from(g)
-    objective = O.OBJ_LAPLACIAN if name in ("signed", "torus") else O.OBJ_MULTILINEAR01
-    mu = 0.9 if C != 128 else 0.0
-    y, v = _blocks(g, C, ld, precision, 9, mu)
-    kern = REG | deco.DECO_KERNEL_PIPE_ENTRIES(entries) | deco.DECO_KERNEL_PIPE_MIXED_ADD
-    for steps in (3, 4):
-        ref = _phase(G, y, v, C, ld, steps, objective, precision, 0.01, mu, deco.DECO_KERNEL_GLOBAL)
-        got = _phase(G, y, v, C, ld, steps, objective, precision, 0.01, mu, kern)
-        _same(ref, got, y, C)
-
-
-@pytest.mark.parametrize("name", ["er800", "signed", "hubs"])
-@pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
-@pytest.mark.parametrize("s", [1, 2, 3])
-def test_register_form_column_slabs_with_budgets_bitwise(name, precision, s):
-    g = GRAPHS[name]()
-    G = deco.graph_from(g)
-    C, ld = 200, 256
-    objective = O.OBJ_LAPLACIAN if name == "signed" else O.OBJ_MULTILINEAR01
-    y, v = _blocks(g, C, ld, precision, 10, 0.9)
-    steps_cols = torch.from_numpy(np.random.default_rng(5).integers(0, 9, C).astype(np.int32)).to(DEV)
-    alpha_cols = torch.from_numpy(np.random.default_rng(6).uniform(1e-3, 2e-2, C).astype(np.float32)).to(DEV)
-    for steps in (7, 8):
-        ref = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9, deco.DECO_KERNEL_GLOBAL,
-                     alpha_cols, steps_cols)
-        got = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9,
-                     REG | deco.DECO_KERNEL_PIPE_ENTRIES(1) | deco.DECO_KERNEL_PIPE_MIXED_ADD
-                     | deco.DECO_KERNEL_PIPE_L2_HINTS | deco.DECO_KERNEL_COLUMN_SLABS(s), alpha_cols, steps_cols)
-        _same(ref, got, y, C)
