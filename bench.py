@@ -61,6 +61,7 @@ ER1M_ALPHA = 0.01
 # A kernel changed since its capture has no entry (traffic reported as null).
 DRAM_TRAFFIC = {
     ("k_slab", 0x20a402): 6759680 + 0,
+    ("k_step_stream", 0x42c00001): 2060485376 + 245023744,
 }
 
 
@@ -337,6 +338,10 @@ def step_kernel_roofline(deco, torch, G, g, sel, stream, steps=100):
     launch shape, timed live: CUDA events on the launching stream around a
     `steps`-step phase of the 128-column BF16 block (after a short warm-up).
 
+    `traffic` is ncu's DRAM read + write bytes of one launch of the kernel in
+    this shape, from the capture summarised with the profiles (null for a
+    shape without one).
+
     Algorithmic bytes per step (all C columns): the CSR once (4 nnz + 4 (n+1))
     plus one read and one write of the BF16 block (2 n C 2 B).  A step of a
     column-slab shape is S launches, each over an n x w slab (w = C / S); the
@@ -356,12 +361,16 @@ def step_kernel_roofline(deco, torch, G, g, sel, stream, steps=100):
     alg = 4 * g.nnz + 4 * (g.n + 1) + 2 * g.n * C * 2
     peaks, kind = measured_peaks()
     ach = alg / t_step / 1e9
-    traffic = DRAM_TRAFFIC.get(("k_step_global", int(sel)))
+    pipelined = bool(sel & deco.DECO_KERNEL_PIPELINED)
+    kname = "k_step_stream" if pipelined else "k_step_global"
+    traffic = DRAM_TRAFFIC.get((kname, int(sel)))
     return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
             "traffic_per": "launch" if traffic is not None else None,
             "peak_kind": kind + " (HBM copy)",
-            "kernel": "k_step_global (fused CSR gather + PGA step, one launch per step and column slab)",
+            "kernel": kname + (" (pipelined form: record streams, cp.async stages; fused gather + PGA step, one launch"
+                               " per step and column slab)" if pipelined else
+                               " (fused CSR gather + PGA step, one launch per step and column slab)"),
             "selector": hex(sel), "launches_per_step": slabs, "us_per_step": t_step * 1e6,
             "us_per_launch": t_step * 1e6 / slabs, "algorithmic_bytes_per_step": alg,
             "algorithmic_bytes_per_launch": alg if slabs == 1 else
