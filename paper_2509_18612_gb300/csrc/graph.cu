@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "deco_internal.cuh"
 
@@ -127,25 +129,45 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
       max_abs_w = std::max(max_abs_w, std::fabs(x));
     }
   }
-  // ---- symmetry: (u,v) present with the same weight as (v,u); binary search in row u
+  // ---- symmetry: (u,v) present with the same weight as (v,u); binary search
+  // in row u.  The rows are split over the host's cores; the error reported is
+  // the one of the lowest row, as a single pass would find it.
   if (!(flags & DECO_GRAPH_SKIP_SYMMETRY_CHECK)) {
-    for (int32_t v = 0; v < n; ++v) {
-      for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-        int32_t u = col_idx[e];
-        int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
-        while (lo < hi) {
-          int32_t mid = lo + (hi - lo) / 2;
-          if (col_idx[mid] < v) lo = mid + 1; else hi = mid;
-        }
-        if (lo >= row_ptr[u + 1] || col_idx[lo] != v) {
-          set_error("asymmetric structure: (%d,%d) stored but (%d,%d) missing", v, u, u, v);
-          return DECO_ERR_GRAPH;
-        }
-        if (weights && weights[lo] != weights[e]) {
-          set_error("asymmetric weights on edge (%d,%d)", v, u);
-          return DECO_ERR_GRAPH;
+    // first offending row of [r0, r1) (its kind in *kind: 1 structure, 2 weights), or r1
+    auto check_rows = [&](int32_t r0, int32_t r1, int* kind, int32_t* bad_u) -> int32_t {
+      for (int32_t v = r0; v < r1; ++v) {
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+          const int32_t u = col_idx[e];
+          int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
+          while (lo < hi) {
+            const int32_t mid = lo + (hi - lo) / 2;
+            if (col_idx[mid] < v) lo = mid + 1; else hi = mid;
+          }
+          if (lo >= row_ptr[u + 1] || col_idx[lo] != v) { *kind = 1; *bad_u = u; return v; }
+          if (weights && weights[lo] != weights[e]) { *kind = 2; *bad_u = u; return v; }
         }
       }
+      return r1;
+    };
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), nnz / 262144 + 1));
+    std::vector<int32_t> first(nt, n);
+    std::vector<int> kinds(nt, 0);
+    std::vector<int32_t> us(nt, 0);
+    auto run = [&](int t) {
+      const int32_t r0 = (int32_t)((int64_t)n * t / nt), r1 = (int32_t)((int64_t)n * (t + 1) / nt);
+      first[t] = check_rows(r0, r1, &kinds[t], &us[t]);
+      if (first[t] == r1) first[t] = n;
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(run, t);
+    run(0);
+    for (auto& th : pool) th.join();
+    for (int t = 0; t < nt; ++t) {
+      if (first[t] >= n) continue;
+      const int32_t v = first[t], u = us[t];
+      if (kinds[t] == 1) set_error("asymmetric structure: (%d,%d) stored but (%d,%d) missing", v, u, u, v);
+      else set_error("asymmetric weights on edge (%d,%d)", v, u);
+      return DECO_ERR_GRAPH;
     }
   }
 

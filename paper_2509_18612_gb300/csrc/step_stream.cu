@@ -392,26 +392,34 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // warps per block: a block fits with the momentum slots too; the grid is
-  // sized for the layout without them (the launch of a phase with momentum
-  // then takes a little more than one wave)
+  // Warps per block: every warp keeps its own items in flight, so the shape
+  // that keeps the most warps resident per SM wins (shared memory and
+  // registers decide); a block must also fit with the momentum slots.  The
+  // grid is sized for the layout without them (a phase with momentum then
+  // takes a little more than one wave).
+  void* fn = pick_kernel(prec, sh.G, weighted, sh.acc);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  if (e != cudaSuccess) return cuda_fail(e, "pipelined step shared memory");
+  auto resident = [&](int w, int* per_sm) -> cudaError_t {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, 32 * w, per_warp * w);
+  };
+  int per_sm = 0;
   if (!wpb) {
-    wpb = 8;
-    while (wpb > 1 && per_warp_mom * wpb > (size_t)max_smem) --wpb;
+    int best_warps = 0;
+    for (int w = 8; w >= 1; --w) {
+      if (per_warp_mom * w > (size_t)max_smem) continue;
+      int b = 0;
+      if ((e = resident(w, &b)) != cudaSuccess) return cuda_fail(e, "pipelined step occupancy");
+      if (b * w > best_warps) { best_warps = b * w; wpb = w; per_sm = b; }
+    }
+  } else if (per_warp_mom * wpb <= (size_t)max_smem) {
+    if ((e = resident(wpb, &per_sm)) != cudaSuccess) return cuda_fail(e, "pipelined step occupancy");
   }
-  if (per_warp_mom * wpb > (size_t)max_smem) {
+  if (!wpb || per_warp_mom * wpb > (size_t)max_smem) {
     set_error("the pipelined step kernel does not fit %d warps of %d entries x %d stages", wpb, maxe, stages);
     return DECO_ERR_UNSUPPORTED;
   }
   sh.wpb = wpb;
-  // grid: as many blocks as are resident at once (without momentum slots)
-  void* fn = pick_kernel(prec, sh.G, weighted, sh.acc);
-  const size_t smem = per_warp * wpb;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  if (e != cudaSuccess) return cuda_fail(e, "pipelined step shared memory");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "pipelined step occupancy");
   sh.blocks = std::max(1, per_sm) * device_sm_count();
   sh.nw = sh.blocks * wpb;
   *out = sh;
@@ -432,11 +440,15 @@ int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out) 
   im.gen = gen;
   const int words = 1 + 2 * ng + maxe * ng * (gen ? 2 : 1);
   im.rw = (words + 3) / 4 * 4;
-  // rows by degree, largest first; ties keep the row order
-  std::vector<int32_t> order((size_t)n);
-  std::iota(order.begin(), order.end(), 0);
+  // rows by degree, largest first; ties keep the row order (a counting sort)
   auto deg = [&](int32_t v) { return g->h_row_ptr[v + 1] - g->h_row_ptr[v]; };
-  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
+  int32_t dmax = 0;
+  for (int32_t v = 0; v < n; ++v) dmax = std::max(dmax, deg(v));
+  std::vector<int64_t> start((size_t)dmax + 2, 0);
+  for (int32_t v = 0; v < n; ++v) ++start[(size_t)(dmax - deg(v)) + 1];
+  for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
+  std::vector<int32_t> order((size_t)n);
+  for (int32_t v = 0; v < n; ++v) order[(size_t)start[(size_t)(dmax - deg(v))]++] = v;
   const int32_t nslices = (n + ng - 1) / ng;
   // records per warp: slice s belongs to warp s mod nw, its parts consecutive
   std::vector<int64_t> count((size_t)im.nw + 1, 0);
