@@ -357,7 +357,7 @@ def step_kernel_roofline(deco, torch, G, g, sel, stream, steps=100):
     k1.record(stream)
     torch.cuda.synchronize()
     t_step = k0.elapsed_time(k1) / 1e3 / steps
-    slabs = 1 << ((sel >> 16) & 0xF) if (sel & 0xFF) == deco.DECO_KERNEL_GLOBAL and (sel >> 16) & 0xF else 1
+    slabs = 1 << ((sel >> 16) & 0xF) if (sel & 0x3) == deco.DECO_KERNEL_GLOBAL and (sel >> 16) & 0xF else 1
     alg = 4 * g.nnz + 4 * (g.n + 1) + 2 * g.n * C * 2
     peaks, kind = measured_peaks()
     ach = alg / t_step / 1e9
@@ -502,7 +502,7 @@ def run_er4096_dense():
     C = DENSE_B
     BF, MUL = deco.DECO_PREC_BF16, deco.DECO_OBJ_MULTILINEAR01
     sel, us_probe = deco.deco_autotune(G, C, BF, MUL, 0.0, 20)
-    dense_sel = sel if (sel & 0xFF) == deco.DECO_KERNEL_DENSE else deco.DECO_KERNEL_DENSE
+    dense_sel = sel if (sel & 0x3) == deco.DECO_KERNEL_DENSE else deco.DECO_KERNEL_DENSE
     sched = [(1, DENSE_STEPS, DENSE_ALPHA, 0.0)]
 
     def solve(kernel, precision, seed=2):

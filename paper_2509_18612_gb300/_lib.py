@@ -52,6 +52,7 @@ DECO_KERNEL_ROW_PAIRS = 1 << 21
 DECO_KERNEL_PIPELINED = 1 << 22
 DECO_KERNEL_PIPE_MIXED_ADD = 1 << 30
 DECO_KERNEL_PIPE_L2_HINTS = 1 << 19
+DECO_KERNEL_PIPE_WIDE = 1 << 2
 
 
 def DECO_KERNEL_PIPE_ENTRIES(e: int) -> int:

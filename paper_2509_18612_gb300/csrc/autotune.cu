@@ -51,14 +51,20 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
   for (int s = 1; s <= 4; ++s) cands.push_back(DECO_KERNEL_GLOBAL | (s << 16));   // 2..16 column slabs
   // the pipelined per-step form (record streams, cp.async stages), with the
   // mixed-precision BF16 add: 8 / 12 / 16 entries per item and 2 stages, or 8
-  // entries and 3 stages, on the whole block and on 2 or 4 column slabs (the
-  // shapes that measured competitive on a 10^6-node graph)
+  // entries and 3 stages, on the whole block and on 2 or 4 column slabs; the
+  // wide form (two vectors per lane) of the 8- and 12-entry shapes on the
+  // whole block and on 2 slabs (the shapes that measured competitive on a
+  // 10^6-node graph)
   for (int s = 0; s <= 2; ++s) {
     for (int e : {1, 3, 0})
       cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(e) |
                       DECO_KERNEL_PIPE_STAGES(1) | DECO_KERNEL_PIPE_MIXED_ADD);
     cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(1) |
                     DECO_KERNEL_PIPE_STAGES(0) | DECO_KERNEL_PIPE_MIXED_ADD);
+    if (s <= 1)
+      for (int e : {1, 3})
+        cands.push_back(DECO_KERNEL_GLOBAL | (s << 16) | DECO_KERNEL_PIPELINED | DECO_KERNEL_PIPE_ENTRIES(e) |
+                        DECO_KERNEL_PIPE_STAGES(1) | DECO_KERNEL_PIPE_MIXED_ADD | DECO_KERNEL_PIPE_WIDE);
   }
   for (int k = 1; k <= 8; k *= 2)
     for (int t = 1; t <= 2; ++t)
@@ -71,7 +77,7 @@ extern "C" int deco_autotune(const deco_graph* g, int32_t C, int32_t precision, 
   for (int k = 1; k <= 8; k *= 2) cands.push_back(DECO_KERNEL_ONCHIP | (k << 8) | (2 << 12) | (2 << 14) | DECO_KERNEL_LEAN);
   // every on-chip shape also in the row-pair form (a half-warp per row)
   for (size_t i = 0, n0 = cands.size(); i < n0; ++i)
-    if ((cands[i] & 0xFF) == DECO_KERNEL_ONCHIP) cands.push_back(cands[i] | DECO_KERNEL_ROW_PAIRS);
+    if ((cands[i] & 0x3) == DECO_KERNEL_ONCHIP) cands.push_back(cands[i] | DECO_KERNEL_ROW_PAIRS);
   // dense tensor-core kernel: BF16 blocks of graphs with at least n^2 / 64 entries
   if (precision == DECO_PREC_BF16 && (double)g->nnz * 64.0 >= (double)g->n * (double)g->n)
     for (int k = 1; k <= 8; k *= 2) cands.push_back(DECO_KERNEL_DENSE | (k << 8));

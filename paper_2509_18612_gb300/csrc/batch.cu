@@ -586,7 +586,7 @@ extern "C" int deco_solve_batch(const deco_batch* b, int32_t B, const deco_param
       lanes.emplace_back(new Lane());
       lanes.back()->lift = pop->lifts[i];
       if ((rc = lanes.back()->R.prepare(U, B * pop->lifts[i], ld, p->precision, p->kernel, st))) return rc;
-      const int kind = p->kernel & 0xFF;
+      const int kind = p->kernel & 0x3;
       if ((kind == DECO_KERNEL_AUTO || kind == DECO_KERNEL_ONCHIP) &&
           (rc = batch_slab_prepare(b, B * pop->lifts[i], ld, p->precision, ybuf[0],
                                    pop->momentum != 0.0f ? vbuf : nullptr, pop->momentum != 0.0f, alpha_cols,

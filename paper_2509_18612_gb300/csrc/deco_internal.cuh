@@ -84,6 +84,8 @@ struct StreamShape {
   bool weighted = false, gen = false;
   int acc = 0;         // BF16 unit-weight sums: 0 widen + add, 1 mixed-precision add
   bool hints = false;  // records and new rows evict-first in L2
+  int U = 1;           // 16-byte vectors per lane (2: the wide form)
+  int fe = 0;          // entries per item fixed at compile time (8 or 12, two stages), or 0
 };
 
 // The opaque handle of the ABI.
@@ -184,9 +186,9 @@ int launch_step_global(const StepLaunch& s, cudaStream_t st);
 // The pipelined form of the same step (bit-identical iterates): the shape
 // for a block of C columns (stream_shape, which also sizes the grid), the
 // graph's record streams for that shape (stream_image), one launch.
-int stream_group_lanes(int32_t C, int prec);
+int stream_group_lanes(int32_t C, int prec, int U);
 int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weighted, bool gen, bool mixed,
-                 bool hints, StreamShape* out);
+                 bool hints, bool wide, StreamShape* out);
 int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out);
 void free_stream_image(StreamImage& im);
 int launch_step_stream(const StepLaunch& s, const StreamImage& im, const StreamShape& sh, cudaStream_t st);

@@ -62,7 +62,7 @@ static double onchip_cost(int64_t own_nnz, int32_t own, int32_t n, int k, int wa
 }
 
 bool valid_selector(int kernel) {
-  const int kind = kernel & 0xFF, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
+  const int kind = kernel & 0x3, k = (kernel >> 8) & 0xF, t = (kernel >> 12) & 0x3, x = (kernel >> 14) & 0x3;
   const int s = (kernel >> 16) & 0x7;
   const int l2hints = (kernel >> 19) & 1;
   const int lean = (kernel >> 20) & 1;
@@ -70,7 +70,10 @@ bool valid_selector(int kernel) {
   const int pipe = (kernel >> 22) & 1;
   const int pipe_shape = (kernel >> 23) & 0x7F;   // entries, stages, warps
   const int mixed = (kernel >> 30) & 1;
+  const int wide = (kernel >> 2) & 1;
   if (kernel & ~0x7FFFFFFF) return false;
+  if (kernel & 0xF8) return false;   // bits 3..7 are not defined
+  if (wide && !pipe) return false;
   if (mixed && !pipe) return false;
   if (l2hints && !pipe) return false;
   if (pipe && ((pipe_shape >> 2) & 3) == 3) return false;   // stage code 3 is not defined
@@ -170,10 +173,11 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
   const bool want_pipe = ((force >> 22) & 1) != 0;
   const int pipe_e = (force >> 23) & 3, pipe_s = (force >> 25) & 3, pipe_w = (force >> 27) & 7;
   const bool pipe_mix = ((force >> 30) & 1) != 0;
+  const bool pipe_wide = ((force >> 2) & 1) != 0;
   // the row-pair form is also the cost model's choice (measured faster on
   // every on-chip shape of the benchmark); the autotuner times both forms
-  const bool want_pairs = ((force >> 21) & 1) != 0 || (force & 0xFF) == DECO_KERNEL_AUTO;
-  force &= 0xFF;
+  const bool want_pairs = ((force >> 21) & 1) != 0 || (force & 0x3) == DECO_KERNEL_AUTO;
+  force &= 0x3;
   if (force == DECO_KERNEL_DENSE) {
     // BF16 blocks only; an FP32 block (e.g. the FP32 polish) is planned as AUTO
     if (prec != DECO_PREC_BF16) return plan_phase(g, C, ld, prec, DECO_KERNEL_AUTO, plan);
@@ -202,7 +206,7 @@ int plan_phase(const deco_graph* g, int32_t C, int32_t ld, int prec, int force, 
       const int cols = plan->col_slabs > 1 ? plan->slab_w : C;
       const bool weighted = g->wmode != W_UNIT, gen = g->wmode == W_GENERAL;
       int rc = stream_shape(cols, prec, entries[pipe_e], stages[pipe_s], pipe_w, weighted, gen, pipe_mix, want_hints,
-                            &plan->stream);
+                            pipe_wide, &plan->stream);
       if (rc) return rc;
     }
     return DECO_OK;

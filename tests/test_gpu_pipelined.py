@@ -6,8 +6,10 @@ value must be bit-identical to it -- on graphs with hubs (rows split into
 several parts), +-1 and general integral weights, isolated nodes, ragged and
 wide column counts (several column chunks), per-column step sizes and step
 budgets, both objectives, with and without momentum, every stage shape and
-with column slabs.  The lane-group form itself is checked against the FP64
-oracle step by step in test_gpu_parity.py.
+with column slabs; in the form with the shape read from the arguments, the
+forms with 8 or 12 entries per item fixed at compile time, and the wide form
+(two 16-byte vectors per lane).  The lane-group form itself is checked
+against the FP64 oracle step by step in test_gpu_parity.py.
 """
 import numpy as np
 import pytest
@@ -26,6 +28,10 @@ import paper_2509_18612_gb300 as deco  # noqa: E402
 DEV = torch.device("cuda:0")
 OBJ = {O.OBJ_MULTILINEAR01: deco.DECO_OBJ_MULTILINEAR01, O.OBJ_LAPLACIAN: deco.DECO_OBJ_LAPLACIAN}
 PIPE = deco.DECO_KERNEL_GLOBAL | deco.DECO_KERNEL_PIPELINED
+FIX8 = PIPE | deco.DECO_KERNEL_PIPE_ENTRIES(1) | deco.DECO_KERNEL_PIPE_STAGES(1)    # 8 entries, 2 stages
+FIX12 = PIPE | deco.DECO_KERNEL_PIPE_ENTRIES(3) | deco.DECO_KERNEL_PIPE_STAGES(1)   # 12 entries, 2 stages
+WIDE = deco.DECO_KERNEL_PIPE_WIDE
+FORMS = {"runtime": PIPE, "fixed8": FIX8, "fixed12": FIX12, "wide8": FIX8 | WIDE, "wide12": FIX12 | WIDE}
 
 
 def _signed(n, p, seed, choices):
@@ -95,10 +101,13 @@ def _same(ref, got, y0, C):
         assert torch.equal(got[1][:, :C], ref[1][:, :C])
 
 
+@pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
 @pytest.mark.parametrize("C,ld", [(128, 128), (203, 256), (24, 64), (520, 576)])
-def test_pipelined_step_bitwise_equals_lane_groups(name, precision, C, ld):
+def test_pipelined_step_bitwise_equals_lane_groups(form, name, precision, C, ld):
+    # (520 columns: several column chunks; 203: a ragged chunk whose second
+    # vectors in the wide form lie partly or wholly past C)
     g = GRAPHS[name]()
     G = deco.graph_from(g)
     objective = O.OBJ_LAPLACIAN if name in ("signed", "torus") else O.OBJ_MULTILINEAR01
@@ -106,17 +115,26 @@ def test_pipelined_step_bitwise_equals_lane_groups(name, precision, C, ld):
     y, v = _blocks(g, C, ld, precision, 3, mu)
     for steps in (3, 4):                              # odd / even: the result in either buffer
         ref = _phase(G, y, v, C, ld, steps, objective, precision, 0.01, mu, deco.DECO_KERNEL_GLOBAL)
-        got = _phase(G, y, v, C, ld, steps, objective, precision, 0.01, mu, PIPE)
+        got = _phase(G, y, v, C, ld, steps, objective, precision, 0.01, mu, FORMS[form])
         _same(ref, got, y, C)
 
 
 @pytest.mark.parametrize("entries", [0, 1, 2, 3])
 @pytest.mark.parametrize("stages", [0, 1, 2, 3])
 @pytest.mark.parametrize("warps", [0, 1, 3])
-def test_pipelined_shapes_bitwise(entries, stages, warps):
+@pytest.mark.parametrize("wide", [False, True])
+def test_pipelined_shapes_bitwise(entries, stages, warps, wide):
     # every entries-per-item / stage-count / block shape on the graph with
     # rows of up to 300 entries (up to 38 parts of 8); stage code 3 is not
-    # defined and is refused
+    # defined and is refused, and the wide form runs only with 8 or 12
+    # entries in 2 stages
+    fixed = stages == 1 and entries in (1, 3)
+    if wide and stages != 3 and not fixed:
+        with pytest.raises(deco.DecoError):
+            deco.deco_run_phase(deco.graph_from(GRAPHS["er800"]()), 64, 64, torch.zeros(800, 64, device=DEV), None,
+                                1, deco.step_args(), PIPE | WIDE | deco.DECO_KERNEL_PIPE_ENTRIES(entries)
+                                | deco.DECO_KERNEL_PIPE_STAGES(stages))
+        return
     if stages == 3:
         with pytest.raises(deco.DecoError):
             deco.deco_run_phase(deco.graph_from(GRAPHS["er800"]()), 64, 64, torch.zeros(800, 64, device=DEV), None,
@@ -127,7 +145,7 @@ def test_pipelined_shapes_bitwise(entries, stages, warps):
     G = deco.graph_from(g)
     C, ld = 128, 128
     kern = (PIPE | deco.DECO_KERNEL_PIPE_ENTRIES(entries) | deco.DECO_KERNEL_PIPE_STAGES(stages)
-            | deco.DECO_KERNEL_PIPE_WARPS(warps))
+            | deco.DECO_KERNEL_PIPE_WARPS(warps) | (WIDE if wide else 0))
     for precision in (deco.DECO_PREC_FP32, deco.DECO_PREC_BF16):
         y, v = _blocks(g, C, ld, precision, 4, 0.9)
         ref = _phase(G, y, v, C, ld, 5, O.OBJ_MULTILINEAR01, precision, 0.01, 0.9, deco.DECO_KERNEL_GLOBAL)
@@ -138,8 +156,8 @@ def test_pipelined_shapes_bitwise(entries, stages, warps):
 @pytest.mark.parametrize("name", ["er800", "signed", "ba", "hubs"])
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
 @pytest.mark.parametrize("s", [1, 2])
-@pytest.mark.parametrize("hints", [False, True])
-def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, hints):
+@pytest.mark.parametrize("form", ["runtime", "hints", "fixed8", "wide8", "wide12"])
+def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, form):
     # column slabs, per-column step sizes and budgets; with and without the L2
     # eviction priorities (a cache hint changes no value)
     g = GRAPHS[name]()
@@ -153,7 +171,8 @@ def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, hints):
         ref = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9, deco.DECO_KERNEL_GLOBAL,
                      alpha_cols, steps_cols)
         got = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9,
-                     PIPE | deco.DECO_KERNEL_COLUMN_SLABS(s) | (deco.DECO_KERNEL_PIPE_L2_HINTS if hints else 0),
+                     (PIPE | deco.DECO_KERNEL_PIPE_L2_HINTS if form == "hints" else FORMS[form])
+                     | deco.DECO_KERNEL_COLUMN_SLABS(s),
                      alpha_cols, steps_cols)
         _same(ref, got, y, C)
 
@@ -166,8 +185,9 @@ def test_pipelined_nonfinite_flag_and_single_node():
     C = ld = 64
     y, _ = _blocks(g, C, ld, deco.DECO_PREC_FP32, 1, 0.0)
     y[5, 3] = float("inf")
-    _, _, flag = _phase(G, y, None, C, ld, 1, O.OBJ_MULTILINEAR01, deco.DECO_PREC_FP32, 0.01, 0.0, PIPE)
-    assert flag & 1
+    for kern in FORMS.values():
+        _, _, flag = _phase(G, y, None, C, ld, 1, O.OBJ_MULTILINEAR01, deco.DECO_PREC_FP32, 0.01, 0.0, kern)
+        assert flag & 1
     one = deco.graph_from(gg.from_edges(1, [], []))
     y1 = torch.full((1, 64), 0.5, device=DEV)
     got = _phase(one, y1, None, 64, 64, 3, O.OBJ_MULTILINEAR01, deco.DECO_PREC_FP32, 0.01, 0.0, PIPE)
@@ -179,19 +199,20 @@ def test_pipelined_solve_equals_lane_group_solve():
     G = deco.graph_from(g)
     sched = [(1, 60, 0.01, 0.9), (2, 20, 0.001, 0.9)]
     out = []
-    for kern in (deco.DECO_KERNEL_GLOBAL, PIPE, PIPE | deco.DECO_KERNEL_COLUMN_SLABS(1)):
+    for kern in (deco.DECO_KERNEL_GLOBAL, PIPE, PIPE | deco.DECO_KERNEL_COLUMN_SLABS(1), FIX8 | WIDE):
         for prec in (deco.DECO_PREC_FP32, deco.DECO_PREC_BF16):
             res, z, pc = deco.deco_solve(G, 64, sched, deco.params(init=deco.DECO_INIT_IDI, precision=prec,
                                                                     kernel=kern), 3)
             out.append((prec, res.best_cut, res.best_init, res.best_phase, z.tobytes(), pc.tobytes()))
     for prec in (deco.DECO_PREC_FP32, deco.DECO_PREC_BF16):
         runs = [o[1:] for o in out if o[0] == prec]
-        assert runs[0] == runs[1] == runs[2]
+        assert runs[0] == runs[1] == runs[2] == runs[3]
 
 
 @pytest.mark.parametrize("name", ["er800", "ba", "hubs", "isolated", "er_sparse"])
 @pytest.mark.parametrize("C,ld", [(128, 128), (203, 256), (24, 64)])
-def test_pipelined_mixed_precision_add_bitwise(name, C, ld):
+@pytest.mark.parametrize("form", ["runtime", "fixed8", "fixed12", "wide8", "wide12"])
+def test_pipelined_mixed_precision_add_bitwise(name, C, ld, form):
     # BF16 sums of unit-weight rows with the mixed-precision add instruction:
     # the same value as widening the BF16 operand and adding in FP32
     g = GRAPHS[name]()
@@ -199,7 +220,7 @@ def test_pipelined_mixed_precision_add_bitwise(name, C, ld):
     y, v = _blocks(g, C, ld, deco.DECO_PREC_BF16, 6, 0.9)
     ref = _phase(G, y, v, C, ld, 5, O.OBJ_MULTILINEAR01, deco.DECO_PREC_BF16, 0.01, 0.9, deco.DECO_KERNEL_GLOBAL)
     got = _phase(G, y, v, C, ld, 5, O.OBJ_MULTILINEAR01, deco.DECO_PREC_BF16, 0.01, 0.9,
-                 PIPE | deco.DECO_KERNEL_PIPE_MIXED_ADD)
+                 FORMS[form] | deco.DECO_KERNEL_PIPE_MIXED_ADD)
     _same(ref, got, y, C)
 
 
