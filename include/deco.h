@@ -156,9 +156,9 @@ typedef enum deco_status {
  *                                1: 2, 2: 4
  *   DECO_KERNEL_PIPE_WARPS(w)    warps per block: w = 0: as many as fit
  *                                (at most 8), 1..7: w
- * The shapes with 8 or 12 entries in 2 stages (without L2 hints) run a form
- * of the kernel compiled for that shape (loops fully unrolled); the others
- * read the shape at run time. */
+ * The shapes with 8 or 12 entries in 2 stages run a form of the kernel
+ * compiled for that shape (loops fully unrolled); the others read the shape
+ * at run time. */
 #define DECO_KERNEL_PIPELINED (1 << 22)
 #define DECO_KERNEL_PIPE_ENTRIES(e) ((e) << 23)
 #define DECO_KERNEL_PIPE_STAGES(s) ((s) << 25)
@@ -174,8 +174,7 @@ typedef enum deco_status {
 /* With DECO_KERNEL_PIPELINED: the wide form, each lane carrying two 16-byte
  * vectors of its row, so an item holds twice the rows for the same columns
  * (half the items per step).  Runs the shapes with 8 or 12 entries per item
- * in 2 stages without DECO_KERNEL_PIPE_L2_HINTS (DECO_ERR_UNSUPPORTED
- * otherwise).  Same iterates. */
+ * in 2 stages (DECO_ERR_UNSUPPORTED otherwise).  Same iterates. */
 #define DECO_KERNEL_PIPE_WIDE (1 << 2)
 
 /* deco_create_graph flags */

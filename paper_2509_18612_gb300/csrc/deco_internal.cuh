@@ -7,8 +7,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <deque>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "deco.h"
@@ -16,6 +18,20 @@
 #include <nvtx3/nvToolsExt.h>
 
 namespace deco {
+
+// Runs f(t, r0, r1) on nt host threads over consecutive ranges [r0, r1) of
+// [0, n) (thread 0 is the caller), nt chosen from `work` (about 2^18 units per
+// thread, at most the host's cores).  Returns nt; f's ranges are in order of t.
+template <class F>
+int host_parallel(int64_t n, int64_t work, F&& f) {
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({hw, work / 262144 + 1, std::max<int64_t>(n, 1)}));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back([&f, t, n, nt] { f(t, n * t / nt, n * (t + 1) / nt); });
+  f(0, (int64_t)0, n / nt);
+  for (auto& th : pool) th.join();
+  return nt;
+}
 
 // NVTX range on the calling host thread for the lifetime of the object (the
 // enqueue of a solve, a phase, its steps and its rounding), so that a

@@ -86,7 +86,10 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
   if (!row_ptr) { set_error("row_ptr is NULL"); return DECO_ERR_ARG; }
   if (nnz > 0 && !col_idx) { set_error("col_idx is NULL"); return DECO_ERR_ARG; }
 
-  // ---- structure
+  // ---- structure: row_ptr non-decreasing first (so every row's entries lie
+  // inside col_idx), then the entries of all rows, split over the host's
+  // cores; the error reported is the one of the lowest row, as a single pass
+  // would find it.
   if (row_ptr[0] != 0) { set_error("row_ptr[0] = %d, expected 0", row_ptr[0]); return DECO_ERR_GRAPH; }
   if ((int64_t)row_ptr[n] != nnz) {
     set_error("row_ptr[n] = %d, expected nnz = %lld", row_ptr[n], (long long)nnz);
@@ -97,14 +100,26 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
       set_error("row_ptr decreases at row %d", v);
       return DECO_ERR_GRAPH;
     }
-    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-      int32_t u = col_idx[e];
-      if (u < 0 || u >= n) { set_error("col_idx[%d] = %d out of range (row %d)", e, u, v); return DECO_ERR_GRAPH; }
-      if (u == v) { set_error("self loop at row %d", v); return DECO_ERR_GRAPH; }
-      if (!device_order && e > row_ptr[v] && col_idx[e - 1] >= u) {
-        set_error("row %d: column indices not strictly increasing at entry %d", v, e);
-        return DECO_ERR_GRAPH;
+  }
+  {
+    struct Bad { int32_t row = -1, e = 0, u = 0, kind = 0; };   // kind 1 range, 2 self loop, 3 order
+    std::vector<Bad> bad(std::max<unsigned>(1, std::thread::hardware_concurrency()));
+    host_parallel(n, nnz, [&](int t, int64_t r0, int64_t r1) {
+      for (int32_t v = (int32_t)r0; v < (int32_t)r1; ++v) {
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+          const int32_t u = col_idx[e];
+          const int kind = (u < 0 || u >= n) ? 1 : u == v ? 2
+                           : (!device_order && e > row_ptr[v] && col_idx[e - 1] >= u) ? 3 : 0;
+          if (kind) { bad[t] = Bad{v, e, u, kind}; return; }
+        }
       }
+    });
+    for (const Bad& b : bad) {
+      if (b.row < 0) continue;
+      if (b.kind == 1) set_error("col_idx[%d] = %d out of range (row %d)", b.e, b.u, b.row);
+      else if (b.kind == 2) set_error("self loop at row %d", b.row);
+      else set_error("row %d: column indices not strictly increasing at entry %d", b.row, b.e);
+      return DECO_ERR_GRAPH;
     }
   }
   // ---- weights: nonzero integers, |w| <= 2^20 (exact in FP32 sums and in int cut sums)
@@ -149,19 +164,14 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
       }
       return r1;
     };
-    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), nnz / 262144 + 1));
-    std::vector<int32_t> first(nt, n);
-    std::vector<int> kinds(nt, 0);
-    std::vector<int32_t> us(nt, 0);
-    auto run = [&](int t) {
-      const int32_t r0 = (int32_t)((int64_t)n * t / nt), r1 = (int32_t)((int64_t)n * (t + 1) / nt);
-      first[t] = check_rows(r0, r1, &kinds[t], &us[t]);
-      if (first[t] == r1) first[t] = n;
-    };
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nt; ++t) pool.emplace_back(run, t);
-    run(0);
-    for (auto& th : pool) th.join();
+    const int hw = (int)std::max<unsigned>(1, std::thread::hardware_concurrency());
+    std::vector<int32_t> first(hw, n);
+    std::vector<int> kinds(hw, 0);
+    std::vector<int32_t> us(hw, 0);
+    const int nt = host_parallel(n, nnz, [&](int t, int64_t r0, int64_t r1) {
+      first[t] = check_rows((int32_t)r0, (int32_t)r1, &kinds[t], &us[t]);
+      if (first[t] == (int32_t)r1) first[t] = n;
+    });
     for (int t = 0; t < nt; ++t) {
       if (first[t] >= n) continue;
       const int32_t v = first[t], u = us[t];
@@ -183,23 +193,38 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
   g->h_row_ptr.assign(row_ptr, row_ptr + (size_t)n + 1);
   std::vector<int32_t> deg(n);
   std::vector<float> dnet(n);
-  for (int32_t v = 0; v < n; ++v) {
-    deg[v] = row_ptr[v + 1] - row_ptr[v];
-    g->deg_s1 += deg[v];
-    g->deg_s2 += (int64_t)deg[v] * deg[v];
-    if (deg[v] > g->max_deg) g->max_deg = deg[v];
-    double s = 0.0, sabs = 0.0;
-    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-      s += weights ? weights[e] : 1.0;
-      sabs += weights ? std::fabs(weights[e]) : 1.0;
+  {
+    // degrees, their sums and maximum, net weighted degrees; per thread, then
+    // combined in thread order (integer sums: the same totals in any order)
+    struct Part { int64_t s1 = 0, s2 = 0; int32_t maxd = 0, bad = -1; double sabs = 0.0; };
+    std::vector<Part> part(std::max<unsigned>(1, std::thread::hardware_concurrency()));
+    const int nt = host_parallel(n, nnz, [&](int t, int64_t r0, int64_t r1) {
+      Part& P = part[t];
+      for (int32_t v = (int32_t)r0; v < (int32_t)r1; ++v) {
+        deg[v] = row_ptr[v + 1] - row_ptr[v];
+        P.s1 += deg[v];
+        P.s2 += (int64_t)deg[v] * deg[v];
+        P.maxd = std::max(P.maxd, deg[v]);
+        double s = 0.0, sabs = 0.0;
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+          s += weights ? weights[e] : 1.0;
+          sabs += weights ? std::fabs(weights[e]) : 1.0;
+        }
+        if (sabs > 16777216.0 && P.bad < 0) { P.bad = v; P.sabs = sabs; }
+        dnet[v] = (float)s;   // integral and |s| <= 2^24: exact in FP32
+      }
+    });
+    for (int t = 0; t < nt; ++t) {
+      if (part[t].bad >= 0) {
+        set_error("row %d: sum of |w| = %g exceeds 2^24 (FP32 sums of binary iterates "
+                  "would no longer be exact)", part[t].bad, part[t].sabs);
+        delete g;
+        return DECO_ERR_UNSUPPORTED;
+      }
+      g->deg_s1 += part[t].s1;
+      g->deg_s2 += part[t].s2;
+      g->max_deg = std::max(g->max_deg, part[t].maxd);
     }
-    if (sabs > 16777216.0) {
-      set_error("row %d: sum of |w| = %g exceeds 2^24 (FP32 sums of binary iterates "
-                "would no longer be exact)", v, sabs);
-      delete g;
-      return DECO_ERR_UNSUPPORTED;
-    }
-    dnet[v] = (float)s;   // integral and |s| <= 2^24: exact in FP32
   }
 
   // ---- device upload
@@ -229,7 +254,10 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
     }
   }
   int rc = up((void**)&g->row_ptr, row_ptr, sizeof(int32_t) * (size_t)(n + 1));
-  if (rc == DECO_OK) rc = up((void**)&g->col_idx, g->h_col.data(), sizeof(int32_t) * (size_t)nnz);
+  // the caller's indices where the device order is theirs (a pinned caller
+  // buffer then uploads at full link speed)
+  if (rc == DECO_OK)
+    rc = up((void**)&g->col_idx, g->wmode == W_SIGN ? g->h_col.data() : col_idx, sizeof(int32_t) * (size_t)nnz);
   if (rc == DECO_OK) rc = up((void**)&g->deg, deg.data(), sizeof(int32_t) * (size_t)n);
   if (rc == DECO_OK) rc = up((void**)&g->dnet, dnet.data(), sizeof(float) * (size_t)n);
   if (rc == DECO_OK && g->wmode == W_SIGN) {

@@ -2,6 +2,8 @@
 // shape, the per-warp record streams of a graph, and the launch.
 #include <algorithm>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -28,6 +30,9 @@ void stream_sizes(int G, int U, int prec, int maxe, int stages, bool mom, bool g
   const int NG = 32 / G, VN = prec == DECO_PREC_BF16 ? 8 : 4, W = 16 * G * U;
   *rw = stream_record_words(NG, maxe, gen);
   *group = (uint32_t)(maxe + 1) * W + (mom ? (uint32_t)(G * U * VN * 4) : 0u);
+  // with two lanes per row, the four groups that one 128-byte shared-memory
+  // wavefront serves must start in distinct 32-byte bank windows
+  if (G == 2 && *group % 64 == 0) *group += 32;
   *stage = (uint32_t)NG * *group;
   *per_warp = (size_t)2 * stages * *rw * 4 + (size_t)stages * *stage;
 }
@@ -35,12 +40,12 @@ void stream_sizes(int G, int U, int prec, int maxe, int stages, bool mom, bool g
 }  // namespace
 
 // lanes per row segment for C columns and U vectors per lane: enough lanes
-// for the row's 16-byte vectors, at least 4, at most 32 (wider blocks run as
-// column chunks of 32 U vectors)
+// for the row's 16-byte vectors, at least 4 (2 in the wide form), at most 32
+// (wider blocks run as column chunks of 32 U vectors)
 int stream_group_lanes(int32_t C, int prec, int U) {
   const int VN = prec == DECO_PREC_BF16 ? 8 : 4;
   const int lanes = ((C + VN - 1) / VN + U - 1) / U;
-  int G = 4;
+  int G = U == 2 ? 2 : 4;
   while (G < lanes && G < 32) G <<= 1;
   return G;
 }
@@ -52,11 +57,11 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
     return DECO_ERR_ARG;
   }
   StreamShape sh;
-  // the compile-time form where the shape has one: 8 or 12 entries, 2 stages, no hints
-  sh.fe = (!hints && stages == 2 && (maxe == 8 || maxe == 12)) ? maxe : 0;
+  // the compile-time form where the shape has one: 8 or 12 entries, 2 stages
+  sh.fe = (stages == 2 && (maxe == 8 || maxe == 12)) ? maxe : 0;
   sh.U = wide ? 2 : 1;
   if (wide && !sh.fe) {
-    set_error("the wide pipelined step runs 8 or 12 entries per item in 2 stages without L2 hints");
+    set_error("the wide pipelined step runs 8 or 12 entries per item in 2 stages");
     return DECO_ERR_UNSUPPORTED;
   }
   sh.G = stream_group_lanes(C, prec, sh.U);
@@ -80,6 +85,10 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
   // grid is sized for the layout without them (a phase with momentum then
   // takes a little more than one wave).
   void* fn = pick_kernel(prec, sh.G, weighted, sh.acc, sh.U, sh.fe);
+  if (!fn) {
+    set_error("pipelined step: no kernel for %d lanes per row and %d vectors per lane", sh.G, sh.U);
+    return DECO_ERR_UNSUPPORTED;
+  }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   if (e != cudaSuccess) return cuda_fail(e, "pipelined step shared memory");
   auto resident = [&](int w, int* per_sm) -> cudaError_t {
@@ -149,44 +158,57 @@ int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out) 
     set_error("the pipelined step kernel's records exceed 2^31 words (n=%d)", n);
     return DECO_ERR_UNSUPPORTED;
   }
-  std::vector<uint32_t> rec((size_t)std::max<int64_t>(acc, 1) * im.rw, 0u);
-  std::vector<int64_t> fill(soff.begin(), soff.end());
-  for (int32_t s = 0; s < nslices; ++s) {
-    const int w = s % im.nw;
-    const int parts = parts_of(s);
-    for (int p = 0; p < parts; ++p) {
-      uint32_t* r = rec.data() + (size_t)fill[w]++ * im.rw;
-      int kmax = 0;
-      for (int i = 0; i < ng; ++i) {
-        const int64_t rr = (int64_t)s * ng + i;
-        const int32_t v = rr < n ? order[rr] : -1;
-        const int32_t d = v >= 0 ? deg(v) : 0;
-        const int32_t cnt = std::max(0, std::min(maxe, d - p * maxe));
-        kmax = std::max(kmax, cnt);
-        r[1 + i] = (uint32_t)v;
-        r[1 + ng + i] = (uint32_t)cnt | (p == 0 ? 0x10000u : 0u) | (p == parts - 1 ? 0x20000u : 0u);
-        const int32_t e0 = v >= 0 ? g->h_row_ptr[v] + p * maxe : 0;
-        for (int k = 0; k < maxe; ++k) {
-          uint32_t c = REC_PAD;
-          float wt = 0.0f;
-          if (k < cnt) {
-            c = (uint32_t)g->h_col[e0 + k];
-            if (sgn && g->h_w[e0 + k] < 0.0f) c |= 0x80000000u;
-            if (gen) wt = g->h_w[e0 + k];
+  // every word of every record is written below (no zero fill); the warps'
+  // streams are filled in parallel, each thread a consecutive range of warps
+  const size_t rec_words = (size_t)std::max<int64_t>(acc, 1) * im.rw;
+  std::unique_ptr<uint32_t[]> rec(new (std::nothrow) uint32_t[rec_words]);
+  if (!rec) {
+    set_error("host allocation of the pipelined step kernel's records failed");
+    return DECO_ERR_OOM;
+  }
+  if (acc == 0) std::fill(rec.get(), rec.get() + rec_words, 0u);
+  const int words = 1 + 2 * ng + maxe * ng * (gen ? 2 : 1);
+  host_parallel(im.nw, acc * im.rw, [&](int, int64_t w0, int64_t w1) {
+    for (int64_t w = w0; w < w1; ++w) {
+      int64_t fill = soff[w];
+      for (int64_t s = w; s < nslices; s += im.nw) {
+        const int parts = parts_of((int32_t)s);
+        for (int p = 0; p < parts; ++p) {
+          uint32_t* r = rec.get() + (size_t)fill++ * im.rw;
+          int kmax = 0;
+          for (int i = 0; i < ng; ++i) {
+            const int64_t rr = s * ng + i;
+            const int32_t v = rr < n ? order[rr] : -1;
+            const int32_t d = v >= 0 ? deg(v) : 0;
+            const int32_t cnt = std::max(0, std::min(maxe, d - p * maxe));
+            kmax = std::max(kmax, cnt);
+            r[1 + i] = (uint32_t)v;
+            r[1 + ng + i] = (uint32_t)cnt | (p == 0 ? 0x10000u : 0u) | (p == parts - 1 ? 0x20000u : 0u);
+            const int32_t e0 = v >= 0 ? g->h_row_ptr[v] + p * maxe : 0;
+            for (int k = 0; k < maxe; ++k) {
+              uint32_t c = REC_PAD;
+              float wt = 0.0f;
+              if (k < cnt) {
+                c = (uint32_t)g->h_col[e0 + k];
+                if (sgn && g->h_w[e0 + k] < 0.0f) c |= 0x80000000u;
+                if (gen) wt = g->h_w[e0 + k];
+              }
+              r[1 + 2 * ng + k * ng + i] = c;
+              if (gen) {
+                uint32_t u;
+                memcpy(&u, &wt, 4);
+                r[1 + 2 * ng + maxe * ng + k * ng + i] = u;
+              }
+            }
           }
-          r[1 + 2 * ng + k * ng + i] = c;
-          if (gen) {
-            uint32_t u;
-            memcpy(&u, &wt, 4);
-            r[1 + 2 * ng + maxe * ng + k * ng + i] = u;
-          }
+          r[0] = (uint32_t)kmax;
+          for (int k = words; k < im.rw; ++k) r[k] = 0u;   // padding
         }
       }
-      r[0] = (uint32_t)kmax;
     }
-  }
-  cudaError_t e = cudaMalloc((void**)&im.rec, rec.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpy(im.rec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice);
+  });
+  cudaError_t e = cudaMalloc((void**)&im.rec, rec_words * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(im.rec, rec.get(), rec_words * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&im.soff, soff.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(im.soff, soff.data(), soff.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {

@@ -37,8 +37,8 @@
 //
 // FE > 0 fixes the entries per item (FE) and the stages (2) at compile time:
 // the per-entry loops unroll completely and the shapes' runtime arithmetic
-// folds away.  Shapes with other entry or stage counts, or with the L2
-// eviction hints, run the FE = 0 form, which reads them from the arguments.
+// folds away.  Shapes with other entry or stage counts run the FE = 0 form,
+// which reads them from the arguments.
 #pragma once
 
 #include <cstdint>
@@ -151,7 +151,7 @@ __host__ __device__ constexpr int stream_record_words(int ng, int maxe, bool gen
 // ACC: how the BF16 rows of unit-weight graphs are summed (the same value
 // either way): 0 widened and added in FP32, 1 with the mixed-precision add.
 // U: 16-byte vectors per lane (1 or 2).  FE: entries per item fixed at
-// compile time (two stages, no L2 hints), or 0 (shape from the arguments).
+// compile time (two stages), or 0 (shape from the arguments).
 template <int PREC, int G, bool WT, int ACC, int U, int FE>
 __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ Str
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int g = lane / G, j = lane % G;
   const int S = FE ? 2 : a.stages, RR = 2 * S, MAXE = FE ? FE : a.maxe, RW = a.rw;
-  const bool hints = FE ? false : a.hints != 0;
+  const bool hints = a.hints != 0;
   const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
   const int32_t i0 = __ldg(a.soff + warp);
   const int32_t m = __ldg(a.soff + warp + 1) - i0;   // records of this warp
@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(256) k_step_stream(const __grid_constant__ Str
       const uint32_t dst = wsm_s + (uint32_t)sf * rec_bytes;
       const uint32_t* src = wrec + (size_t)pf.r * RW;
       if (FE && RWMAX <= 128) {
-        if (lane * 4 < RW) cp16(dst + (uint32_t)lane * 16u, src + lane * 4);
+        if (lane * 4 < RW) {
+          if (hints) cp16_hint(dst + (uint32_t)lane * 16u, src + lane * 4, pol_first);
+          else cp16(dst + (uint32_t)lane * 16u, src + lane * 4);
+        }
       } else {
         for (int l = lane; l * 4 < RW; l += 32) {
           if (hints) cp16_hint(dst + (uint32_t)l * 16u, src + l * 4, pol_first);
@@ -396,6 +399,9 @@ void* stream_kernel_wt(bool wt, int acc) {
 template <int PREC, int U, int FE>
 void* stream_kernel_g(int G, bool wt, int acc) {
   switch (G) {
+    case 2:   // two lanes per row: the wide form only
+      if constexpr (U == 2) return stream_kernel_wt<PREC, 2, U, FE>(wt, acc);
+      return nullptr;
     case 4: return stream_kernel_wt<PREC, 4, U, FE>(wt, acc);
     case 8: return stream_kernel_wt<PREC, 8, U, FE>(wt, acc);
     case 16: return stream_kernel_wt<PREC, 16, U, FE>(wt, acc);

@@ -156,13 +156,15 @@ def test_pipelined_shapes_bitwise(entries, stages, warps, wide):
 @pytest.mark.parametrize("name", ["er800", "signed", "ba", "hubs"])
 @pytest.mark.parametrize("precision", [deco.DECO_PREC_FP32, deco.DECO_PREC_BF16])
 @pytest.mark.parametrize("s", [1, 2])
-@pytest.mark.parametrize("form", ["runtime", "hints", "fixed8", "wide8", "wide12"])
-def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, form):
+@pytest.mark.parametrize("form", ["runtime", "runtime_hints", "fixed8", "fixed8_hints", "wide8", "wide12_hints"])
+@pytest.mark.parametrize("C,ld", [(200, 256), (128, 128)])
+def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, form, C, ld):
     # column slabs, per-column step sizes and budgets; with and without the L2
-    # eviction priorities (a cache hint changes no value)
+    # eviction priorities (a cache hint changes no value).  200 columns: a
+    # ragged last slab; 128 columns in 4 slabs: two lanes per row in the wide
+    # form
     g = GRAPHS[name]()
     G = deco.graph_from(g)
-    C, ld = 200, 256                                  # ragged last slab
     objective = O.OBJ_LAPLACIAN if name == "signed" else O.OBJ_MULTILINEAR01
     y, v = _blocks(g, C, ld, precision, 4, 0.9)
     steps_cols = torch.from_numpy(np.random.default_rng(5).integers(0, 9, C).astype(np.int32)).to(DEV)
@@ -171,8 +173,8 @@ def test_pipelined_column_slabs_with_budgets_bitwise(name, precision, s, form):
         ref = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9, deco.DECO_KERNEL_GLOBAL,
                      alpha_cols, steps_cols)
         got = _phase(G, y, v, C, ld, steps, objective, precision, 0.0, 0.9,
-                     (PIPE | deco.DECO_KERNEL_PIPE_L2_HINTS if form == "hints" else FORMS[form])
-                     | deco.DECO_KERNEL_COLUMN_SLABS(s),
+                     FORMS[form.replace("_hints", "")] | deco.DECO_KERNEL_COLUMN_SLABS(s)
+                     | (deco.DECO_KERNEL_PIPE_L2_HINTS if form.endswith("_hints") else 0),
                      alpha_cols, steps_cols)
         _same(ref, got, y, C)
 
