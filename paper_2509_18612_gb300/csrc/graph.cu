@@ -72,6 +72,35 @@ extern "C" int deco_create_graph(int32_t n, int64_t nnz, const int32_t* row_ptr,
   return deco::create_graph_impl(n, nnz, row_ptr, col_idx, weights, flags, false, out);
 }
 
+namespace {
+
+// The lowest row v that stores an entry (v, u) whose mirror (u, v) is
+// missing (binary search of row u), into *bad_row (atomicMin; left alone when
+// every entry has its mirror).  One warp per row, its lanes over the row's
+// entries; the indices are already known to lie in [0, n).
+__global__ void k_symmetry(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           int32_t* bad_row) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    bool miss = false;
+    const int32_t e1 = rp[v + 1];
+    for (int32_t e = rp[v] + lane; e < e1; e += 32) {
+      const int32_t u = ci[e];
+      int32_t lo = rp[u], hi = rp[u + 1];
+      const int32_t end = hi;
+      while (lo < hi) {
+        const int32_t mid = lo + (hi - lo) / 2;
+        if (ci[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= end || ci[lo] != (int32_t)v) miss = true;
+    }
+    if (__any_sync(0xFFFFFFFFu, miss) && lane == 0) atomicMin(bad_row, (int32_t)v);
+  }
+}
+
+}  // namespace
+
 // `device_order`: the rows come from validated graphs in device edge order
 // (a +-1 row lists its positive entries first), so sortedness is not checked.
 int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
@@ -145,25 +174,28 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
     }
   }
   // ---- symmetry: (u,v) present with the same weight as (v,u); binary search
-  // in row u.  The rows are split over the host's cores; the error reported is
-  // the one of the lowest row, as a single pass would find it.
-  if (!(flags & DECO_GRAPH_SKIP_SYMMETRY_CHECK)) {
-    // first offending row of [r0, r1) (its kind in *kind: 1 structure, 2 weights), or r1
-    auto check_rows = [&](int32_t r0, int32_t r1, int* kind, int32_t* bad_u) -> int32_t {
-      for (int32_t v = r0; v < r1; ++v) {
-        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-          const int32_t u = col_idx[e];
-          int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
-          while (lo < hi) {
-            const int32_t mid = lo + (hi - lo) / 2;
-            if (col_idx[mid] < v) lo = mid + 1; else hi = mid;
-          }
-          if (lo >= row_ptr[u + 1] || col_idx[lo] != v) { *kind = 1; *bad_u = u; return v; }
-          if (weights && weights[lo] != weights[e]) { *kind = 2; *bad_u = u; return v; }
+  // in row u.  Large graphs of unit weights (nnz >= 2^20) are checked on the
+  // device after the upload (k_symmetry); the others here, the rows split
+  // over the host's cores.  Either way the error reported is the one of the
+  // lowest row, as a single pass would find it.
+  // first offending row of [r0, r1) (its kind in *kind: 1 structure, 2 weights), or r1
+  auto check_rows = [&](int32_t r0, int32_t r1, int* kind, int32_t* bad_u) -> int32_t {
+    for (int32_t v = r0; v < r1; ++v) {
+      for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const int32_t u = col_idx[e];
+        int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
+        while (lo < hi) {
+          const int32_t mid = lo + (hi - lo) / 2;
+          if (col_idx[mid] < v) lo = mid + 1; else hi = mid;
         }
+        if (lo >= row_ptr[u + 1] || col_idx[lo] != v) { *kind = 1; *bad_u = u; return v; }
+        if (weights && weights[lo] != weights[e]) { *kind = 2; *bad_u = u; return v; }
       }
-      return r1;
-    };
+    }
+    return r1;
+  };
+  const bool device_check = (!weights || all_unit) && nnz >= ((int64_t)1 << 20);
+  if (!(flags & DECO_GRAPH_SKIP_SYMMETRY_CHECK) && !device_check) {
     const int hw = (int)std::max<unsigned>(1, std::thread::hardware_concurrency());
     std::vector<int32_t> first(hw, n);
     std::vector<int> kinds(hw, 0);
@@ -272,6 +304,28 @@ int deco::create_graph_impl(int32_t n, int64_t nnz, const int32_t* row_ptr, cons
     std::vector<int32_t> wi((size_t)nnz);
     for (int64_t e = 0; e < nnz; ++e) wi[e] = (int32_t)g->h_w[e];
     rc = up((void**)&g->wint, wi.data(), sizeof(int32_t) * (size_t)nnz);
+  }
+  if (rc == DECO_OK && !(flags & DECO_GRAPH_SKIP_SYMMETRY_CHECK) && device_check) {
+    int32_t* d_bad = nullptr;
+    int32_t bad = n;
+    cudaError_t e = cudaMalloc((void**)&d_bad, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_bad, &bad, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)n + 7) / 8, 4096);
+      k_symmetry<<<blocks, 256>>>(n, g->row_ptr, g->col_idx, d_bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "symmetry check");
+    } else if (bad < n) {
+      int kind = 0;
+      int32_t u = 0;
+      check_rows(bad, bad + 1, &kind, &u);   // the offending entry of that row, for the message
+      set_error("asymmetric structure: (%d,%d) stored but (%d,%d) missing", bad, u, u, bad);
+      rc = DECO_ERR_GRAPH;
+    }
   }
   if (rc != DECO_OK) {
     free_graph(g);

@@ -151,3 +151,30 @@ def test_injected_scratch_allocation_failures_leave_the_library_usable():
     finally:
         deco.deco_debug_fail_scratch_alloc(0)
     assert failed >= 10, failed
+
+
+@pytest.mark.parametrize("where", ["first", "middle", "last", "none"])
+def test_large_graph_symmetry_check_on_the_device(where):
+    # graphs of unit weights with nnz >= 2^20 are checked for symmetry on the
+    # device: a removed mirror entry is reported at the lowest offending row,
+    # as the host check reports it on small graphs; a symmetric graph passes
+    g = gg.er_graph_avg_degree(120_000, 10, 6)
+    rp, ci = g.row_ptr.astype(np.int32), g.col_idx.astype(np.int32)
+    assert ci.size >= 1 << 20
+    if where != "none":
+        v = {"first": 0, "middle": g.n // 2, "last": g.n - 1}[where]
+        while rp[v + 1] == rp[v]:
+            v += 1
+        e = rp[v + 1] - 1                              # drop the last entry (v, u) of row v
+        u = int(ci[e])
+        ci = np.delete(ci, e)
+        rp = rp.copy()
+        rp[v + 1:] -= 1
+        # (u, v) is now the one entry without a mirror: row u is the offending row
+        with pytest.raises(deco.DecoError) as ei:
+            deco.deco_create_graph(g.n, rp, ci, None)
+        assert ei.value.status == deco.DECO_ERR_GRAPH
+        assert f"({u},{v}) stored but ({v},{u}) missing" in deco.last_error(), deco.last_error()
+    else:
+        G = deco.deco_create_graph(g.n, rp, ci, None)
+        G.close()
