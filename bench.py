@@ -688,7 +688,25 @@ def run_ba256():
             "device_s": res.device_ms / 1e3, "wall_s": t, "sum_best_cuts": int(best.sum()),
             "sum_m": int(sum(g.m for g in graphs_)), "gpu_launches": res.kernel_launches,
             "final_alpha": [float(10 ** x) for x in ex["final_e"][:4]], "final_T": ex["final_T"][:4].tolist(),
-            "round_best_score": [int(s.max()) for s in ex["round_scores"]]}
+            "round_best_score": [int(s.max()) for s in ex["round_scores"]],
+            "roofline": batched_roofline(res)}
+
+
+def batched_roofline(res):
+    """Roofline of the batched search: every edge-update of an on-chip phase
+    reads one FP32 replica word from shared memory, so the gathered bytes are
+    4 x edge-updates; the time is the whole solve's device time (all rounds,
+    the ranking and evolution kernels included), against the derived
+    shared-memory load path of the SMs."""
+    peaks, kind = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_onchip = 152 * 128 * sm_mhz * 1e6 / 1e9
+    gathered = 4.0 * res.edge_updates
+    ach = gathered / (res.device_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
+            "traffic": None, "kernel": "k_slab (batched: one item per graph and column slab)",
+            "algorithmic_bytes": gathered, "time_s": res.device_ms / 1e3,
+            "peak_kind": "derived: 152 SMs x 128 B/clk (shared-memory load path) x sm_max_mhz (" + kind + " clock)"}
 
 
 def run_ba16_cut_gap():

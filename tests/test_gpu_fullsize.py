@@ -160,13 +160,21 @@ def test_er1m_pipelined_form_bitwise_equals_lane_groups(er1m, precision):
     y0 = (torch.rand(g.n, C, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3)) * 2 - 1).to(dt)
     a = deco.step_args(MUL, precision, 0.01, 0.0)
     pipe = deco.DECO_KERNEL_GLOBAL | deco.DECO_KERNEL_PIPELINED
+    # the compiled 8-entry, 2-stage shape with the mixed-precision add, one and
+    # two vectors per lane (the benchmark's tuned shape is the wide one), on
+    # the whole block and on 2 and 4 column slabs
+    fixed8 = (pipe | deco.DECO_KERNEL_PIPE_ENTRIES(1) | deco.DECO_KERNEL_PIPE_STAGES(1)
+              | deco.DECO_KERNEL_PIPE_MIXED_ADD)
+    wide = deco.DECO_KERNEL_PIPE_WIDE
     out = []
-    for kern in (deco.DECO_KERNEL_GLOBAL, pipe, pipe | deco.DECO_KERNEL_COLUMN_SLABS(2)):
+    for kern in (deco.DECO_KERNEL_GLOBAL, pipe, pipe | deco.DECO_KERNEL_COLUMN_SLABS(2), fixed8, fixed8 | wide,
+                 fixed8 | wide | deco.DECO_KERNEL_COLUMN_SLABS(1), fixed8 | wide | deco.DECO_KERNEL_COLUMN_SLABS(2)):
         y = y0.clone()
         deco.deco_run_phase(G, C, C, y, None, 10, a, kern)
         torch.cuda.synchronize()
         out.append(y)
-    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+    for k in range(1, len(out)):
+        assert torch.equal(out[0], out[k]), k
 
 
 @pytest.mark.parametrize("which", ["ba2000", "er5000"])
