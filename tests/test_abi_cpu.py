@@ -115,3 +115,33 @@ def test_fault_injection_hook_arguments(deco):
         deco.deco_debug_fail_scratch_alloc(-1)
     assert ei.value.status == deco.DECO_ERR_ARG
     deco.deco_debug_fail_scratch_alloc(0)
+
+
+def test_threaded_validation_reports_the_lowest_offending_row(deco):
+    # a graph large enough that the host checks run on several threads
+    # (2 M entries): two planted errors in different threads' row ranges; the
+    # message must name the lower row, as a single pass would
+    g = gg.er_graph_avg_degree(200_000, 10, 21)
+    rp, ci = g.row_ptr.astype(np.int32), g.col_idx.astype(np.int32).copy()
+    lo_row, hi_row = 30_001, 170_003
+    for v in (lo_row, hi_row):
+        assert rp[v + 1] > rp[v]
+    ci[rp[hi_row]] = hi_row                     # self loop in a late row
+    ci[rp[lo_row + 1] - 1] = g.n + 5            # out-of-range index in an earlier row
+    with pytest.raises(deco.DecoError) as ei:
+        deco.deco_create_graph(g.n, rp, ci, None)
+    assert ei.value.status == deco.DECO_ERR_GRAPH
+    assert f"(row {lo_row})" in deco.last_error(), deco.last_error()
+    # weighted symmetry (checked on the host): asymmetric weights planted in two rows
+    ci = g.col_idx.astype(np.int32)
+    w = np.ones(ci.size, np.float32)
+    for v in (hi_row, lo_row):
+        e = rp[v]
+        u = int(ci[e])
+        w[e] = 2.0                                 # (v, u) weighs 2, its mirror (u, v) 1
+        w[rp[u]:rp[u + 1]][ci[rp[u]:rp[u + 1]] == v] = 1.0
+    first = min(min(hi_row, int(ci[rp[hi_row]])), min(lo_row, int(ci[rp[lo_row]])))
+    with pytest.raises(deco.DecoError) as ei:
+        deco.deco_create_graph(g.n, rp, ci, w)
+    assert ei.value.status == deco.DECO_ERR_GRAPH
+    assert f"asymmetric weights on edge ({first}," in deco.last_error(), deco.last_error()
