@@ -142,6 +142,21 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+_SMEM_PEAK = {}
+
+
+def smem_peak(deco):
+    """The shared-memory load path of all SMs in GB/s, measured live by the
+    library's probe (the larger of its 8- and 16-byte word rates; taken once
+    per process), and the derived figure 152 SMs x 128 B/clk x the measured
+    maximum SM clock beside it."""
+    if "gbs" not in _SMEM_PEAK:
+        _SMEM_PEAK["gbs"] = max(deco.deco_probe_smem_rate(16, 1 << 16), deco.deco_probe_smem_rate(8, 1 << 16))
+    peaks, kind = measured_peaks()
+    derived = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    return _SMEM_PEAK["gbs"], derived, kind
+
+
 def whole_job(ms_local: float, units_per_rank: float, world: int, device="cpu"):
     """Timed milliseconds as the maximum over the ranks (replicas run the same
     work), and the whole-job rate: the units every rank processed / that time."""
@@ -275,8 +290,8 @@ def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
 
     Algorithmic bytes per launch = steps x nnz x C x element size: every
     stored CSR entry reads one neighbour's row segment from the on-chip
-    replica.  The bound is the SM load path (shared memory): 152 SMs x 128
-    bytes per clock."""
+    replica.  The bound is the SM load path (shared memory), measured by the
+    library's probe; 152 SMs x 128 bytes per clock is its derived ceiling."""
     C = B
     ld = C
     prec = deco.DECO_PREC_BF16 if args.precision == "bf16" else deco.DECO_PREC_FP32
@@ -302,9 +317,7 @@ def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
     t = statistics.median(times)
     gathered = g.nnz * C * esz * ROOF_STEPS
     compulsory = 2 * g.n * C * (esz + 4) + (g.n + 1 + g.nnz) * 4
-    peaks, kind = measured_peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_onchip = 152 * 128 * sm_mhz * 1e6 / 1e9      # GB/s through the SM load path
+    peak_onchip, derived, kind = smem_peak(deco)      # GB/s through the SM load path
     ach = gathered / t / 1e9
     sel = tuned_selector_hint
     return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
@@ -313,8 +326,9 @@ def roofline_step(args, deco, torch, dev, G, g, tuned_selector_hint=None):
             "kernel": "k_slab (persistent on-chip PGA phase, fused gather + step)", "selector": sel,
             "launch_us": t * 1e6, "steps_per_launch": ROOF_STEPS, "us_per_step": t * 1e6 / ROOF_STEPS,
             "algorithmic_bytes_per_launch": gathered, "compulsory_dram_bytes_per_launch": compulsory,
-            "peak_kind": "derived: 152 SMs x 128 B/clk (shared-memory load path) x sm_max_mhz ("
-                         + kind + " clock)"}
+            "peak_kind": "measured: deco_probe_smem_rate (shared-memory load path, all SMs)",
+            "derived_peak": derived, "frac_of_derived": ach / derived,
+            "derived_peak_kind": "152 SMs x 128 B/clk x sm_max_mhz (" + kind + " clock)"}
 
 
 def run_reference(args, rank, world):
@@ -696,17 +710,18 @@ def batched_roofline(res):
     """Roofline of the batched search: every edge-update of an on-chip phase
     reads one FP32 replica word from shared memory, so the gathered bytes are
     4 x edge-updates; the time is the whole solve's device time (all rounds,
-    the ranking and evolution kernels included), against the derived
-    shared-memory load path of the SMs."""
-    peaks, kind = measured_peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_onchip = 152 * 128 * sm_mhz * 1e6 / 1e9
+    the ranking and evolution kernels included), against the shared-memory
+    load path of the SMs (measured by the library's probe)."""
+    import paper_2509_18612_gb300 as deco
+    peak_onchip, derived, kind = smem_peak(deco)
     gathered = 4.0 * res.edge_updates
     ach = gathered / (res.device_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": ach, "peak": peak_onchip, "unit": "GB/s", "frac": ach / peak_onchip,
             "traffic": None, "kernel": "k_slab (batched: one item per graph and column slab)",
             "algorithmic_bytes": gathered, "time_s": res.device_ms / 1e3,
-            "peak_kind": "derived: 152 SMs x 128 B/clk (shared-memory load path) x sm_max_mhz (" + kind + " clock)"}
+            "peak_kind": "measured: deco_probe_smem_rate (shared-memory load path, all SMs)",
+            "derived_peak": derived, "frac_of_derived": ach / derived,
+            "derived_peak_kind": "152 SMs x 128 B/clk x sm_max_mhz (" + kind + " clock)"}
 
 
 def run_ba16_cut_gap():

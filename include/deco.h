@@ -588,6 +588,16 @@ int deco_local_search(const deco_graph* g, int32_t B, uint8_t* z, int32_t max_ro
  * Errors: DECO_ERR_ARG, DECO_ERR_TIMEOUT (a wait gave up, 1 s), CUDA. */
 int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, float* ns_per_instruction, void* stream);
 
+/* Diagnostic: the shared-memory load bandwidth of the GPU, the ceiling of the
+ * on-chip kernel's gathers (no paper counterpart).  One CTA of 1024 threads
+ * per SM reads `width`-byte words (8 or 16) of a 128 KB shared-memory buffer,
+ * a warp's 32 lanes on consecutive words (no bank conflicts), `iters` words
+ * per thread (a multiple of 8, at most 2^24).  gbs (host) receives the bytes
+ * read by all SMs divided by the launch's duration (CUDA events, after an
+ * untimed warm-up launch), in GB/s.  Synchronises the stream.
+ * Errors: DECO_ERR_ARG, DECO_ERR_OOM, CUDA. */
+int deco_probe_smem_rate(int32_t width, int32_t iters, float* gbs, void* stream);
+
 /* Failure detection of the bounded device waits.  Every spin-wait of the
  * kernels (the on-chip kernel's exchange wait, the dense kernels' mbarrier
  * waits and grid barrier) gives up after 2 s, sets bit 1 of the call's error

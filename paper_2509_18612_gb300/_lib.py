@@ -83,7 +83,7 @@ EXPORTED = [
     "deco_mpnn_get_params", "deco_mpnn_set_params", "deco_mpnn_infer", "deco_mpnn_loss_grad",
     "deco_mpnn_train_step", "deco_mpnn_train",
     "deco_idi_mean", "deco_dui_mean", "deco_solve", "deco_solve_budget", "deco_greedy", "deco_local_search",
-    "deco_probe_mma_rate", "deco_probe_wait_timeout", "deco_debug_fail_scratch_alloc", "deco_debug_pool_usage",
+    "deco_probe_mma_rate", "deco_probe_smem_rate", "deco_probe_wait_timeout", "deco_debug_fail_scratch_alloc", "deco_debug_pool_usage",
     "deco_last_error", "deco_abi_version",
 ]
 
@@ -168,6 +168,7 @@ def _load():
         "deco_greedy": (ctypes.c_int, [P, I32, U64, P, P, P]),
         "deco_local_search": (ctypes.c_int, [P, I32, P, I32, P, P, P]),
         "deco_probe_mma_rate": (ctypes.c_int, [I32, I32, I32, P, P]),
+        "deco_probe_smem_rate": (ctypes.c_int, [I32, I32, P, P]),
         "deco_probe_wait_timeout": (ctypes.c_int, [I32, P, P]),
         "deco_debug_fail_scratch_alloc": (ctypes.c_int, [I32]),
         "deco_debug_pool_usage": (ctypes.c_int, [P, P, I32]),
@@ -356,6 +357,13 @@ def deco_probe_mma_rate(n: int = 128, issuers: int = 1, count: int = 4096, strea
     ns = ctypes.c_float()
     _check(lib.deco_probe_mma_rate(int(n), int(issuers), int(count), ctypes.byref(ns), _stream(stream)))
     return ns.value
+
+
+def deco_probe_smem_rate(width: int = 16, iters: int = 1 << 16, stream=None) -> float:
+    """Shared-memory load bandwidth of the GPU in GB/s (all SMs; see include/deco.h)."""
+    gbs = ctypes.c_float()
+    _check(lib.deco_probe_smem_rate(int(width), int(iters), ctypes.byref(gbs), _stream(stream)))
+    return gbs.value
 
 
 def deco_probe_wait_timeout(which: int, stream=None):

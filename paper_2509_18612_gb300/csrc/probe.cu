@@ -135,6 +135,83 @@ extern "C" int deco_probe_mma_rate(int32_t n, int32_t issuers, int32_t count, fl
   return DECO_OK;
 }
 
+namespace {
+
+constexpr int SMEM_PROBE_THREADS = 1024;
+constexpr int SMEM_PROBE_BYTES = 131072;  // the buffer every CTA reads (power of two, >= 8 x 1024 x 16 B)
+
+// Shared-memory load bandwidth: every thread reads W-byte words of a 128 KB
+// buffer, the 32 lanes of a warp consecutive words (no bank conflicts), the
+// buffer walked in steps of the CTA's width, `iters` times; the 8 loads of
+// one round are at distinct addresses (so none can be merged with another)
+// and the words are folded into one value per thread, so no load is dropped.
+template <int W>
+__global__ void __launch_bounds__(SMEM_PROBE_THREADS, 1) k_probe_smem(int iters, uint32_t* out) {
+  extern __shared__ __align__(16) unsigned char buf[];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < SMEM_PROBE_BYTES / 4; i += SMEM_PROBE_THREADS)
+    reinterpret_cast<uint32_t*>(buf)[i] = (uint32_t)i * 2654435761u;
+  __syncthreads();
+  uint32_t acc = 0;
+  uint32_t off = (uint32_t)tid * W;
+  constexpr uint32_t STEP = (uint32_t)SMEM_PROBE_THREADS * W, MASK = SMEM_PROBE_BYTES - 1;
+  for (int it = 0; it < iters; it += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint32_t o = (off + (uint32_t)u * STEP) & MASK;
+      if (W == 16) {
+        const uint4 q = *reinterpret_cast<const uint4*>(buf + o);
+        acc ^= q.x ^ q.y ^ q.z ^ q.w;
+      } else {
+        const uint2 q = *reinterpret_cast<const uint2*>(buf + o);
+        acc ^= q.x ^ q.y;
+      }
+    }
+    off = (off + 8u * STEP + (uint32_t)W) & MASK;   // shift by a word each round: no address repeats in order
+  }
+  out[(size_t)blockIdx.x * SMEM_PROBE_THREADS + tid] = acc;
+}
+
+}  // namespace
+
+extern "C" int deco_probe_smem_rate(int32_t width, int32_t iters, float* gbs, void* stream) {
+  clear_error();
+  if ((width != 8 && width != 16) || iters < 8 || iters > (1 << 24) || iters % 8 != 0 || !gbs) {
+    set_error("bad arguments (width=%d iters=%d)", width, iters);
+    return DECO_ERR_ARG;
+  }
+  cudaStream_t st = as_stream(stream);
+  const int sms = device_sm_count();
+  auto fn = width == 16 ? k_probe_smem<16> : k_probe_smem<8>;
+  // the buffer plus enough extra to keep one CTA per SM
+  const size_t smem = SMEM_PROBE_BYTES + 32 * 1024;
+  DECO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  Scratch s(st);
+  uint32_t* d = nullptr;
+  int rc = s.alloc((void**)&d, sizeof(uint32_t) * (size_t)sms * SMEM_PROBE_THREADS);
+  if (rc) return rc;
+  cudaEvent_t ev[2];
+  DECO_CUDA_TRY(cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return cuda_fail(cudaGetLastError(), "event");
+  }
+  fn<<<(unsigned)sms, SMEM_PROBE_THREADS, smem, st>>>(8, d);   // warm-up
+  cudaEventRecord(ev[0], st);
+  fn<<<(unsigned)sms, SMEM_PROBE_THREADS, smem, st>>>(iters, d);
+  cudaEventRecord(ev[1], st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "shared-memory probe");
+  const double bytes = (double)sms * SMEM_PROBE_THREADS * (double)iters * width;
+  *gbs = (float)(bytes / (ms * 1e-3) / 1e9);
+  return DECO_OK;
+}
+
 extern "C" int deco_probe_wait_timeout(int32_t which, float* waited_ms, void* stream) {
   clear_error();
   if (which < 0 || which > 2) {

@@ -145,3 +145,11 @@ def test_threaded_validation_reports_the_lowest_offending_row(deco):
         deco.deco_create_graph(g.n, rp, ci, w)
     assert ei.value.status == deco.DECO_ERR_GRAPH
     assert f"asymmetric weights on edge ({first}," in deco.last_error(), deco.last_error()
+
+
+def test_smem_probe_rejects_bad_arguments(deco):
+    import ctypes
+    gbs = ctypes.c_float()
+    for width, iters in ((4, 64), (16, 0), (16, 12), (8, (1 << 24) + 8)):
+        assert deco.lib.deco_probe_smem_rate(width, iters, ctypes.byref(gbs), None) == deco.DECO_ERR_ARG
+    assert deco.lib.deco_probe_smem_rate(16, 64, None, None) == deco.DECO_ERR_ARG

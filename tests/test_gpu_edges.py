@@ -178,3 +178,13 @@ def test_large_graph_symmetry_check_on_the_device(where):
     else:
         G = deco.deco_create_graph(g.n, rp, ci, None)
         G.close()
+
+
+def test_smem_probe_rate_is_plausible():
+    # the shared-memory load path of all SMs: below the 152 SMs x 128 B/clk
+    # x 2.07 GHz the hardware can deliver at most (plus a margin for the
+    # clock), and well above a tenth of it
+    derived = 152 * 128 * 2.07e9 / 1e9
+    for width in (8, 16):
+        gbs = deco.deco_probe_smem_rate(width, 1 << 14)
+        assert 0.1 * derived < gbs < 1.1 * derived, (width, gbs)
