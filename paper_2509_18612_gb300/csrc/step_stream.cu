@@ -117,13 +117,59 @@ int stream_shape(int32_t C, int prec, int maxe, int stages, int wpb, bool weight
   return DECO_OK;
 }
 
+namespace {
+
+// Fills the records of the per-warp streams: one thread per (slice, row of
+// the slice), writing that row's fields in every part of the slice; the
+// slice's first record is srec[s], its rows order[s ng ...] (-1 past n), its
+// first row the longest (it gives every part's kmax and the number of parts).
+__global__ void k_stream_fill(int32_t n, int32_t nslices, int ng, int maxe, int rw, int wmode, bool gen,
+                              const int32_t* __restrict__ order, const int64_t* __restrict__ srec,
+                              const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                              const uint32_t* __restrict__ col_sw, const float* __restrict__ w, uint32_t* rec) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)nslices * ng) return;
+  const int32_t s = (int32_t)(tid / ng);
+  const int i = (int)(tid % ng);
+  const int64_t rr = (int64_t)s * ng + i;
+  const int32_t v = rr < n ? order[rr] : -1;
+  const int32_t v0 = order[(int64_t)s * ng];
+  const int32_t d0 = row_ptr[v0 + 1] - row_ptr[v0];
+  const int parts = d0 > maxe ? (d0 + maxe - 1) / maxe : 1;
+  const int32_t d = v >= 0 ? row_ptr[v + 1] - row_ptr[v] : 0;
+  const int E0 = 1 + 2 * ng, words = E0 + maxe * ng * (gen ? 2 : 1);
+  for (int p = 0; p < parts; ++p) {
+    uint32_t* r = rec + (size_t)(srec[s] + p) * rw;
+    const int32_t cnt = max(0, min(maxe, d - p * maxe));
+    r[1 + i] = (uint32_t)v;
+    r[1 + ng + i] = (uint32_t)cnt | (p == 0 ? 0x10000u : 0u) | (p == parts - 1 ? 0x20000u : 0u);
+    const int32_t e0 = v >= 0 ? row_ptr[v] + p * maxe : 0;
+    for (int k = 0; k < maxe; ++k) {
+      uint32_t c = REC_PAD;
+      float wt = 0.0f;
+      if (k < cnt) {
+        c = wmode == W_SIGN ? col_sw[e0 + k] : (uint32_t)col_idx[e0 + k];
+        if (gen) wt = w[e0 + k];
+      }
+      r[E0 + k * ng + i] = c;
+      if (gen) r[E0 + maxe * ng + k * ng + i] = __float_as_uint(wt);
+    }
+    if (i == 0) {
+      r[0] = (uint32_t)max(0, min(maxe, d0 - p * maxe));   // kmax: the count of the slice's longest row
+      for (int k = words; k < rw; ++k) r[k] = 0u;           // padding
+    }
+  }
+}
+
+}  // namespace
+
 int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out) {
   const int ng = 32 / sh.G;
   for (auto& im : g->streams)
     if (im.ng == ng && im.maxe == sh.maxe && im.nw == sh.nw && im.gen == sh.gen) { *out = &im; return DECO_OK; }
   const int32_t n = g->n;
   const int maxe = sh.maxe;
-  const bool gen = sh.gen, sgn = g->wmode == W_SIGN;
+  const bool gen = sh.gen;
   StreamImage im;
   im.ng = ng;
   im.maxe = maxe;
@@ -158,57 +204,38 @@ int stream_image(deco_graph* g, const StreamShape& sh, const StreamImage** out) 
     set_error("the pipelined step kernel's records exceed 2^31 words (n=%d)", n);
     return DECO_ERR_UNSUPPORTED;
   }
-  // every word of every record is written below (no zero fill); the warps'
-  // streams are filled in parallel, each thread a consecutive range of warps
-  const size_t rec_words = (size_t)std::max<int64_t>(acc, 1) * im.rw;
-  std::unique_ptr<uint32_t[]> rec(new (std::nothrow) uint32_t[rec_words]);
-  if (!rec) {
-    set_error("host allocation of the pipelined step kernel's records failed");
-    return DECO_ERR_OOM;
-  }
-  if (acc == 0) std::fill(rec.get(), rec.get() + rec_words, 0u);
-  const int words = 1 + 2 * ng + maxe * ng * (gen ? 2 : 1);
-  host_parallel(im.nw, acc * im.rw, [&](int, int64_t w0, int64_t w1) {
-    for (int64_t w = w0; w < w1; ++w) {
-      int64_t fill = soff[w];
-      for (int64_t s = w; s < nslices; s += im.nw) {
-        const int parts = parts_of((int32_t)s);
-        for (int p = 0; p < parts; ++p) {
-          uint32_t* r = rec.get() + (size_t)fill++ * im.rw;
-          int kmax = 0;
-          for (int i = 0; i < ng; ++i) {
-            const int64_t rr = s * ng + i;
-            const int32_t v = rr < n ? order[rr] : -1;
-            const int32_t d = v >= 0 ? deg(v) : 0;
-            const int32_t cnt = std::max(0, std::min(maxe, d - p * maxe));
-            kmax = std::max(kmax, cnt);
-            r[1 + i] = (uint32_t)v;
-            r[1 + ng + i] = (uint32_t)cnt | (p == 0 ? 0x10000u : 0u) | (p == parts - 1 ? 0x20000u : 0u);
-            const int32_t e0 = v >= 0 ? g->h_row_ptr[v] + p * maxe : 0;
-            for (int k = 0; k < maxe; ++k) {
-              uint32_t c = REC_PAD;
-              float wt = 0.0f;
-              if (k < cnt) {
-                c = (uint32_t)g->h_col[e0 + k];
-                if (sgn && g->h_w[e0 + k] < 0.0f) c |= 0x80000000u;
-                if (gen) wt = g->h_w[e0 + k];
-              }
-              r[1 + 2 * ng + k * ng + i] = c;
-              if (gen) {
-                uint32_t u;
-                memcpy(&u, &wt, 4);
-                r[1 + 2 * ng + maxe * ng + k * ng + i] = u;
-              }
-            }
-          }
-          r[0] = (uint32_t)kmax;
-          for (int k = words; k < im.rw; ++k) r[k] = 0u;   // padding
-        }
-      }
+  // the first record of every slice (a slice's parts are consecutive in its
+  // warp's stream); the records themselves are filled on the device
+  std::vector<int64_t> srec((size_t)std::max(nslices, 1), 0);
+  {
+    std::vector<int64_t> fill(soff.begin(), soff.end());
+    for (int32_t s = 0; s < nslices; ++s) {
+      const int w = s % im.nw;
+      srec[(size_t)s] = fill[(size_t)w];
+      fill[(size_t)w] += parts_of(s);
     }
-  });
+  }
+  const size_t rec_words = (size_t)std::max<int64_t>(acc, 1) * im.rw;
+  int32_t* d_order = nullptr;
+  int64_t* d_srec = nullptr;
   cudaError_t e = cudaMalloc((void**)&im.rec, rec_words * 4);
-  if (e == cudaSuccess) e = cudaMemcpy(im.rec, rec.get(), rec_words * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && acc == 0) e = cudaMemset(im.rec, 0, rec_words * 4);
+  if (e == cudaSuccess && nslices > 0) {
+    e = cudaMalloc((void**)&d_order, (size_t)n * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_srec, (size_t)nslices * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(d_order, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_srec, srec.data(), (size_t)nslices * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      const int64_t threads = (int64_t)nslices * ng;
+      k_stream_fill<<<(unsigned)((threads + 255) / 256), 256>>>(n, nslices, ng, maxe, im.rw, g->wmode, gen, d_order,
+                                                                 d_srec, g->row_ptr, g->col_idx, g->col_sw, g->w,
+                                                                 im.rec);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the records outlive this call's ordering
+  }
+  cudaFree(d_order);
+  cudaFree(d_srec);
   if (e == cudaSuccess) e = cudaMalloc((void**)&im.soff, soff.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(im.soff, soff.data(), soff.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
