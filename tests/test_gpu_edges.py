@@ -154,11 +154,14 @@ def test_injected_scratch_allocation_failures_leave_the_library_usable():
 
 
 @pytest.mark.parametrize("where", ["first", "middle", "last", "none"])
-def test_large_graph_symmetry_check_on_the_device(where):
+@pytest.mark.parametrize("family", ["er", "ba"])
+def test_large_graph_symmetry_check_on_the_device(where, family):
     # graphs of unit weights with nnz >= 2^20 are checked for symmetry on the
     # device: a removed mirror entry is reported at the lowest offending row,
-    # as the host check reports it on small graphs; a symmetric graph passes
-    g = gg.er_graph_avg_degree(120_000, 10, 6)
+    # as the host check reports it on small graphs; a symmetric graph passes.
+    # The BA graph's first rows are hubs of hundreds of entries (several
+    # passes of a warp's lanes).
+    g = gg.er_graph_avg_degree(120_000, 10, 6) if family == "er" else gg.ba_graph(140_000, 4, 6)
     rp, ci = g.row_ptr.astype(np.int32), g.col_idx.astype(np.int32)
     assert ci.size >= 1 << 20
     if where != "none":
