@@ -152,13 +152,16 @@ def test_er1m_sparse_fp32_step_matches_oracle(er1m):
     assert np.all(np.abs(out - ref) <= tol)
 
 
-@pytest.mark.parametrize("precision", [deco.DECO_PREC_BF16, deco.DECO_PREC_FP32])
-def test_er1m_pipelined_form_bitwise_equals_lane_groups(er1m, precision):
+@pytest.mark.parametrize("precision,mu", [(deco.DECO_PREC_BF16, 0.0), (deco.DECO_PREC_FP32, 0.0),
+                                          (deco.DECO_PREC_BF16, 0.9)])
+def test_er1m_pipelined_form_bitwise_equals_lane_groups(er1m, precision, mu):
     g, G = er1m
     C = 128
     dt = torch.bfloat16 if precision == deco.DECO_PREC_BF16 else torch.float32
     y0 = (torch.rand(g.n, C, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3)) * 2 - 1).to(dt)
-    a = deco.step_args(MUL, precision, 0.01, 0.0)
+    v0 = (torch.randn(g.n, C, device=DEV, generator=torch.Generator(device=DEV).manual_seed(4)) * 0.1
+          if mu else None)
+    a = deco.step_args(MUL, precision, 0.01, mu)
     pipe = deco.DECO_KERNEL_GLOBAL | deco.DECO_KERNEL_PIPELINED
     # the compiled 8-entry, 2-stage shape with the mixed-precision add, one and
     # two vectors per lane (the benchmark's tuned shape is the wide one), on
@@ -170,11 +173,14 @@ def test_er1m_pipelined_form_bitwise_equals_lane_groups(er1m, precision):
     for kern in (deco.DECO_KERNEL_GLOBAL, pipe, pipe | deco.DECO_KERNEL_COLUMN_SLABS(2), fixed8, fixed8 | wide,
                  fixed8 | wide | deco.DECO_KERNEL_COLUMN_SLABS(1), fixed8 | wide | deco.DECO_KERNEL_COLUMN_SLABS(2)):
         y = y0.clone()
-        deco.deco_run_phase(G, C, C, y, None, 10, a, kern)
+        v = None if v0 is None else v0.clone()
+        deco.deco_run_phase(G, C, C, y, v, 10, a, kern)
         torch.cuda.synchronize()
-        out.append(y)
+        out.append((y, v))
     for k in range(1, len(out)):
-        assert torch.equal(out[0], out[k]), k
+        assert torch.equal(out[0][0], out[k][0]), k
+        if mu:
+            assert torch.equal(out[0][1], out[k][1]), k
 
 
 @pytest.mark.parametrize("which", ["ba2000", "er5000"])
